@@ -1,0 +1,217 @@
+/*
+ * mtp.h - C ABI of the GB300-native Moment Tensor Potential hot path
+ * (the neighborhood-level method of MLIP-3, arXiv 2304.13144).
+ *
+ * Conventions (all entry points):
+ *  - Every array argument is caller-owned.  "device" arrays live in CUDA device memory of
+ *    the current device; "host" arrays in host memory.  The library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is
+ *    enqueued on it; calls that must read a size back from the GPU (neighbor build,
+ *    extraction) synchronise that stream.
+ *  - Handles (mtp_model, mtp_nbr) and their scratch are owned by the library and released
+ *    by mtp_free_model / mtp_free_nbr.
+ *  - No C++ exception crosses the ABI.  A failing call returns a non-zero mtp_status,
+ *    leaves its outputs unspecified and its handles valid; mtp_last_error() gives a
+ *    thread-local message for the last failure on this thread.
+ *  - Parameter layout (the paper fixes none; see the design notes):
+ *      theta = [ s_z (n_types) | xi_a (n_lin, canonical basis order) |
+ *                c[z_i][z_j][mu][beta] (n_types^2 * n_rad * n_q, row-major) ],
+ *    m = n_types + n_lin + n_types^2 n_rad n_q.
+ *  - Units: positions and cells in Angstrom, energies in eV, forces in eV/A,
+ *    virial W_ab = -dE/d(eps_ab) in eV (not divided by the volume).
+ */
+#ifndef MTP_H
+#define MTP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mtp_model mtp_model; /* opaque: descriptor, schedule, parameters, A^-1 */
+typedef struct mtp_nbr mtp_nbr;     /* opaque: neighbor list in device memory */
+
+typedef enum {
+  MTP_OK = 0,
+  MTP_ERR_ARG = 1,         /* invalid argument (null pointer, size, species out of range) */
+  MTP_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  MTP_ERR_CAPACITY = 3,    /* a caller-provided output buffer is too small */
+  MTP_ERR_SINGULAR = 4,    /* active-set matrix singular (LU pivot below tolerance) */
+  MTP_ERR_GEOMETRY = 5,    /* coincident atoms (|r_ij| < 1e-8 A) or a degenerate cell */
+  MTP_ERR_NUMERIC = 6,     /* non-finite input */
+  MTP_ERR_UNSUPPORTED = 7  /* request outside what this build supports */
+} mtp_status;
+
+typedef enum { MTP_FP64 = 0, MTP_MIXED = 1 } mtp_precision;
+
+/* Model descriptor.  Section II.A: n_types species, MTP level lev_max (eqs. 5-6), n_q
+ * radial polynomials (Chebyshev T_0..T_{n_q-1} on [r_min, r_cut], eq. 4), cut-off r_cut. */
+typedef struct {
+  int32_t n_types;
+  int32_t lev_max;
+  int32_t n_q;
+  int32_t reserved;
+  double r_min;
+  double r_cut;
+} mtp_desc;
+
+/* Sizes derived from a descriptor (mtp_describe / mtp_model_sizes). */
+typedef struct {
+  int64_t n_params;     /* m */
+  int32_t n_lin;        /* number of basis functions B_a (eq. 2) */
+  int32_t n_rad;        /* number of radial functions f_mu (eq. 4) */
+  int32_t n_moments;    /* distinct moments M_{mu,nu} used by the basis (eq. 3) */
+  int32_t n_mom_comps;  /* symmetric-storage components of those moments */
+  int32_t n_values;     /* per-atom value array: components + intermediates */
+  int32_t n_triples;    /* flattened contraction triples (dst += c * a * b) */
+  int32_t nu_max;       /* largest tensor rank used */
+  int32_t n_gauge;      /* n_rad (n_rad + 1) / 2 null directions of the parameter rows */
+} mtp_sizes;
+
+/* A batch of configurations (Section III.A: size, types, positions, supercell).
+ * All pointers are caller-owned DEVICE memory. */
+typedef struct {
+  int32_t n_cfg;
+  int32_t reserved;
+  const int64_t* atom_offset; /* n_cfg + 1, atoms of config k are [atom_offset[k], atom_offset[k+1]) */
+  const double* pos;          /* N x 3, A */
+  const int32_t* type;        /* N, 0 .. n_types - 1 */
+  const double* cell;         /* n_cfg x 3 x 3, row a = lattice vector a, A */
+  const uint8_t* pbc;         /* n_cfg x 3, non-zero = periodic along that lattice vector */
+} mtp_batch;
+
+/* ---------------------------------------------------------------------------------- */
+/* Library and model                                                                  */
+/* ---------------------------------------------------------------------------------- */
+
+const char* mtp_version(void);
+const char* mtp_last_error(void); /* thread-local; never NULL */
+
+/* Host-only: sizes of the basis of `desc` (Section II.A, eqs. 5-6).  Calls no CUDA API. */
+mtp_status mtp_describe(const mtp_desc* desc, mtp_sizes* out);
+
+/* Host-only: the canonical basis (Section II.A).  Function a is a multigraph on P[a] <= 4
+ * moment factors with labels (mu[4a+p], nu[4a+p]) and edge multiplicities
+ * edges[6a+e] over node pairs (0,1),(0,2),(0,3),(1,2),(1,3),(2,3).  Arrays are host
+ * memory of capacity n_lin (mu, nu: 4 n_lin; edges: 6 n_lin).  Calls no CUDA API. */
+mtp_status mtp_describe_basis(const mtp_desc* desc, int32_t* P, int32_t* mu, int32_t* nu,
+                              int32_t* edges);
+
+/* Host-only: the flattened contraction schedule (host arrays sized from mtp_sizes):
+ * comp_mu[n_mom_comps], comp_exp[3 n_mom_comps] (exponents a,b,c of x^a y^b z^c),
+ * dst_ptr[n_values - n_mom_comps + 1], tri_a/tri_b[n_triples], tri_c[n_triples],
+ * basis_idx[n_lin].  Value d >= n_mom_comps equals
+ * sum_{t in [dst_ptr[d-n_mom_comps], dst_ptr[d-n_mom_comps+1])} tri_c[t] v[tri_a[t]] v[tri_b[t]].
+ * Calls no CUDA API. */
+mtp_status mtp_describe_schedule(const mtp_desc* desc, int32_t* comp_mu, int32_t* comp_exp,
+                                 int32_t* dst_ptr, int32_t* tri_a, int32_t* tri_b,
+                                 double* tri_c, int32_t* basis_idx);
+
+/* Create a model on the current device.  theta: host, m doubles (layout above).
+ * Enumerates the basis (Section II.A), compiles the contraction schedule and uploads it. */
+mtp_status mtp_load(const mtp_desc* desc, const double* theta, int64_t m, mtp_model** out);
+void mtp_free_model(mtp_model* model);
+int64_t mtp_num_params(const mtp_model* model);
+mtp_status mtp_model_sizes(const mtp_model* model, mtp_sizes* out);
+
+/* Replace theta (host, m doubles); used by training loops (eq. 7). */
+mtp_status mtp_set_params(mtp_model* model, const double* theta, int64_t m);
+
+/* Active set (Sections II.C-D): A is DEVICE memory, m x m row-major FP64, row k = the
+ * parameter row of active-set entry k.  A^-1 is formed on the GPU by FP64 LU with partial
+ * pivoting and kept in the model.  MTP_ERR_SINGULAR if a pivot is below 1e-13 max|A|.
+ * Synchronises `stream`. */
+mtp_status mtp_set_active_set(mtp_model* model, const double* A, int64_t m, void* stream);
+
+/* Copy A^-1 (m x m, row-major FP64) to DEVICE memory `Ainv`. */
+mtp_status mtp_get_active_inverse(const mtp_model* model, double* Ainv, void* stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Neighborhoods                                                                      */
+/* ---------------------------------------------------------------------------------- */
+
+/* Build or rebuild the neighbor list (Section II.A): for every atom i all (j, image n)
+ * with 0 < |r_ij| < r_cut, r_ij = x_j + n.H - x_i, n = 0 along non-periodic axes, by a
+ * cell list over every configuration of the batch.  The full list is kept (both i->j and
+ * j->i), with the index of each pair's reverse.  *inout may be NULL (allocated) or a
+ * previous list (reused, grown if needed).  Synchronises `stream` (sizes are read back).
+ * MTP_ERR_GEOMETRY on coincident atoms or a degenerate cell, MTP_ERR_ARG on a species
+ * outside [0, n_types). */
+mtp_status mtp_build_neighbors(mtp_model* model, const mtp_batch* batch, mtp_nbr** inout,
+                               void* stream);
+void mtp_free_nbr(mtp_nbr* nbr);
+mtp_status mtp_nbr_size(const mtp_nbr* nbr, int64_t* n_atoms, int64_t* n_pairs);
+
+/* Copy the list to DEVICE arrays: off[n_atoms+1], j[n_pairs], image[3 n_pairs] (integer
+ * image n of each pair), r[3 n_pairs] (r_ij, FP64).  Any pointer may be NULL. */
+mtp_status mtp_nbr_export(const mtp_nbr* nbr, const mtp_batch* batch, int64_t* off, int32_t* j,
+                          int32_t* image, double* r, void* stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Hot path                                                                           */
+/* ---------------------------------------------------------------------------------- */
+
+/* Energies, forces and virial (eqs. 1-4; forces and stresses as used by eq. 7).
+ * Outputs are DEVICE memory, any may be NULL except that at least one is given:
+ *   energy[n_cfg] = sum_i V_i per configuration (FP64 accumulation),
+ *   site_energy[N] = V_i, forces[N x 3] = -dE/dx, virial[n_cfg x 9] = -dE/deps (eV).
+ * MTP_MIXED: radial basis, moments, contractions and adjoint in FP32, energy/virial sums
+ * in FP64.  MTP_FP64: everything in FP64.  The neighbor list must have been built for
+ * this batch (same positions for FP64 parity). */
+mtp_status mtp_energy_forces_stress(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                                    mtp_precision prec, double* energy, double* site_energy,
+                                    double* forces, double* virial, void* stream);
+
+/* Per-atom parameter rows b_i = dV_i/dtheta (eq. 9), DEVICE rows[n x m] FP64 for the atoms
+ * listed in DEVICE atoms[n] (atoms == NULL: all atoms, n = N). */
+mtp_status mtp_param_rows(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                          mtp_precision prec, const int64_t* atoms, int64_t n, double* rows,
+                          void* stream);
+
+/* Per-atom extrapolation grade (Section II.D): gamma_i = max_p |(b_i A^-1)_p|,
+ * argmax_i = the lowest p attaining it, and the compacted list of atoms with
+ * gamma_i > threshold (Section II.E, flag iff strictly greater), ascending.
+ * DEVICE outputs: gamma[N] (FP64), argmax[N] or NULL, flagged[N] or NULL,
+ * n_flagged[1] (int64) or NULL.  Requires mtp_set_active_set.  MTP_MIXED forms the
+ * product with split-precision tensor-core arithmetic (FP32-level accuracy); MTP_FP64
+ * in FP64. */
+mtp_status mtp_grade(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                     mtp_precision prec, double threshold, double* gamma, int32_t* argmax,
+                     int32_t* flagged, int64_t* n_flagged, void* stream);
+
+/* One step of MD with extrapolation control (Section III.B): energies, forces, virial and
+ * the grade from a single pass over the neighborhoods.  Arguments as in
+ * mtp_energy_forces_stress and mtp_grade; gamma may be NULL to skip the grade. */
+mtp_status mtp_step(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                    mtp_precision prec, double* energy, double* site_energy, double* forces,
+                    double* virial, double threshold, double* gamma, int32_t* argmax,
+                    int32_t* flagged, int64_t* n_flagged, void* stream);
+
+/* Neighborhoods of selected atoms (Section II.E step 3(ii), Section III.A
+ * cut_extrapolative_neighborhood): for the n DEVICE atom indices idx[], write the
+ * R_cut neighborhood of each as CSR: off[n+1] (int64), then per neighbor its relative
+ * vector r[3] (FP64, A), species type[] and atom index j[] (any of r/type/j may be NULL).
+ * `capacity` is the room in r/type/j (neighbors); *total (host) receives the number of
+ * neighbors.  MTP_ERR_CAPACITY if capacity < total.  Synchronises `stream`. */
+mtp_status mtp_extract_neighborhoods(const mtp_nbr* nbr, const mtp_batch* batch,
+                                     const int32_t* idx, int64_t n, int64_t* off, double* r,
+                                     int32_t* type, int32_t* j, int64_t capacity,
+                                     int64_t* total, void* stream);
+
+/* Loss of eq. 7 and its gradient with respect to theta:
+ *   L = sum_k [ w_e (E_k - E*_k)^2 + w_f sum_i |F_ik - F*_ik|^2 + w_s sum_ab (W_k,ab - W*_k,ab)^2 ].
+ * DEVICE inputs E_ref[n_cfg], F_ref[N x 3], W_ref[n_cfg x 9] (NULL allowed if w_s == 0);
+ * DEVICE outputs loss[1] and grad[m] (FP64).  The force and stress terms use a
+ * forward-over-reverse tangent pass through the hand-written adjoint. */
+mtp_status mtp_train_step(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                          mtp_precision prec, const double* E_ref, const double* F_ref,
+                          const double* W_ref, double w_e, double w_f, double w_s, double* loss,
+                          double* grad, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MTP_H */

@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "mtp_oracle.cpp")
     if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
         tmp = so + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                src, "-o", tmp])
         os.replace(tmp, so)
     return so

@@ -1,0 +1,369 @@
+"""Python binding of the C ABI in include/mtp.h (argument marshalling only).
+
+Every function mirrors the C entry point of the same name; torch tensors supply device
+memory and the current CUDA stream.  The CUDA library must have been built
+(paper_2304_13144_gb300.build.build()); importing this module without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmtp.so")
+
+MTP_FP64 = 0
+MTP_MIXED = 1
+STATUS = {0: "MTP_OK", 1: "MTP_ERR_ARG", 2: "MTP_ERR_CUDA", 3: "MTP_ERR_CAPACITY", 4: "MTP_ERR_SINGULAR",
+          5: "MTP_ERR_GEOMETRY", 6: "MTP_ERR_NUMERIC", 7: "MTP_ERR_UNSUPPORTED"}
+
+
+class MtpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class mtp_desc(ctypes.Structure):
+    _fields_ = [("n_types", ctypes.c_int32), ("lev_max", ctypes.c_int32), ("n_q", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("r_min", ctypes.c_double), ("r_cut", ctypes.c_double)]
+
+
+class mtp_sizes(ctypes.Structure):
+    _fields_ = [("n_params", ctypes.c_int64), ("n_lin", ctypes.c_int32), ("n_rad", ctypes.c_int32),
+                ("n_moments", ctypes.c_int32), ("n_mom_comps", ctypes.c_int32), ("n_values", ctypes.c_int32),
+                ("n_triples", ctypes.c_int32), ("nu_max", ctypes.c_int32), ("n_gauge", ctypes.c_int32)]
+
+
+class mtp_batch(ctypes.Structure):
+    _fields_ = [("n_cfg", ctypes.c_int32), ("reserved", ctypes.c_int32), ("atom_offset", ctypes.c_void_p),
+                ("pos", ctypes.c_void_p), ("type", ctypes.c_void_p), ("cell", ctypes.c_void_p),
+                ("pbc", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_SIGS = {
+    "mtp_version": (ctypes.c_char_p, []),
+    "mtp_last_error": (ctypes.c_char_p, []),
+    "mtp_describe": (ctypes.c_int, [_P, _P]),
+    "mtp_describe_basis": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "mtp_describe_schedule": (ctypes.c_int, [_P] * 8),
+    "mtp_load": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "mtp_free_model": (None, [_P]),
+    "mtp_num_params": (_I64, [_P]),
+    "mtp_model_sizes": (ctypes.c_int, [_P, _P]),
+    "mtp_set_params": (ctypes.c_int, [_P, _P, _I64]),
+    "mtp_set_active_set": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "mtp_get_active_inverse": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_build_neighbors": (ctypes.c_int, [_P, _P, _P, _P]),
+    "mtp_free_nbr": (None, [_P]),
+    "mtp_nbr_size": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_nbr_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "mtp_energy_forces_stress": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "mtp_param_rows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _I64, _P, _P]),
+    "mtp_grade": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _D, _P, _P, _P, _P, _P]),
+    "mtp_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _D, _P, _P, _P, _P, _P]),
+    "mtp_extract_neighborhoods": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _I64, _P, _P]),
+    "mtp_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmtp.so (raises if it was not built: there is no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} missing (run paper_2304_13144_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise MtpError(st, lib().mtp_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    raise TypeError(type(t))
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_desc(n_types, lev_max, n_q=8, r_min=2.0, r_cut=5.0):
+    return mtp_desc(int(n_types), int(lev_max), int(n_q), 0, float(r_min), float(r_cut))
+
+
+# ------------------------------------------------------------------------------------
+# host-only descriptions
+# ------------------------------------------------------------------------------------
+
+def mtp_describe(desc) -> dict:
+    out = mtp_sizes()
+    _check(lib().mtp_describe(ctypes.byref(desc), ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in mtp_sizes._fields_}
+
+
+def mtp_describe_basis(desc):
+    n = mtp_describe(desc)["n_lin"]
+    P = np.zeros(n, np.int32)
+    mu = np.zeros((n, 4), np.int32)
+    nu = np.zeros((n, 4), np.int32)
+    ed = np.zeros((n, 6), np.int32)
+    _check(lib().mtp_describe_basis(ctypes.byref(desc), _ptr(P), _ptr(mu), _ptr(nu), _ptr(ed)))
+    full = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    basis = []
+    for a in range(n):
+        p = int(P[a])
+        labels = tuple((int(mu[a, k]), int(nu[a, k])) for k in range(p))
+        edges = tuple(int(ed[a, full.index((i, j))]) for i in range(p) for j in range(i + 1, p))
+        basis.append((labels, edges))
+    return basis
+
+
+def mtp_describe_schedule(desc) -> dict:
+    sz = mtp_describe(desc)
+    nm, nv, nt, nl = sz["n_mom_comps"], sz["n_values"], sz["n_triples"], sz["n_lin"]
+    out = {"comp_mu": np.zeros(nm, np.int32), "comp_exp": np.zeros((nm, 3), np.int32),
+           "dst_ptr": np.zeros(nv - nm + 1, np.int32), "tri_a": np.zeros(max(nt, 1), np.int32),
+           "tri_b": np.zeros(max(nt, 1), np.int32), "tri_c": np.zeros(max(nt, 1), np.float64),
+           "basis_idx": np.zeros(nl, np.int32)}
+    _check(lib().mtp_describe_schedule(ctypes.byref(desc), *[_ptr(out[k]) for k in
+                                                             ("comp_mu", "comp_exp", "dst_ptr", "tri_a", "tri_b",
+                                                              "tri_c", "basis_idx")]))
+    out["sizes"] = sz
+    return out
+
+
+# ------------------------------------------------------------------------------------
+# handles
+# ------------------------------------------------------------------------------------
+
+class Model:
+    """Owns an mtp_model*."""
+
+    def __init__(self, desc, theta):
+        self.desc = desc
+        theta = np.ascontiguousarray(theta, np.float64)
+        h = ctypes.c_void_p()
+        _check(lib().mtp_load(ctypes.byref(desc), _ptr(theta), theta.size, ctypes.byref(h)))
+        self.h = h
+        self.sizes = self.model_sizes()
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.mtp_free_model(self.h)
+            self.h = None
+
+    @property
+    def n_params(self):
+        return int(lib().mtp_num_params(self.h))
+
+    def model_sizes(self):
+        out = mtp_sizes()
+        _check(lib().mtp_model_sizes(self.h, ctypes.byref(out)))
+        return {k: getattr(out, k) for k, _ in mtp_sizes._fields_}
+
+
+class Batch:
+    """Device copies of a batch (see synth.py for the dict layout) and the mtp_batch struct."""
+
+    def __init__(self, b, device="cuda"):
+        self.atom_offset = torch.as_tensor(np.ascontiguousarray(b["atom_offset"], np.int64), device=device)
+        self.pos = torch.as_tensor(np.ascontiguousarray(b["pos"], np.float64), device=device)
+        self.type = torch.as_tensor(np.ascontiguousarray(b["type"], np.int32), device=device)
+        self.cell = torch.as_tensor(np.ascontiguousarray(b["cell"], np.float64).reshape(-1, 9), device=device)
+        self.pbc = torch.as_tensor(np.ascontiguousarray(b["pbc"], np.uint8).reshape(-1, 3), device=device)
+        self.n_cfg = int(self.atom_offset.numel() - 1)
+        self.n_atoms = int(b["atom_offset"][-1])
+        self.refresh()
+
+    def refresh(self):
+        self.c = mtp_batch(self.n_cfg, 0, self.atom_offset.data_ptr(), self.pos.data_ptr(), self.type.data_ptr(),
+                           self.cell.data_ptr(), self.pbc.data_ptr())
+        return self
+
+
+class Neighbors:
+    """Owns an mtp_nbr*."""
+
+    def __init__(self):
+        self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.mtp_free_nbr(self.h)
+            self.h = ctypes.c_void_p()
+
+    def size(self):
+        na, npairs = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().mtp_nbr_size(self.h, ctypes.byref(na), ctypes.byref(npairs)))
+        return na.value, npairs.value
+
+
+# ------------------------------------------------------------------------------------
+# entry points
+# ------------------------------------------------------------------------------------
+
+def mtp_load(desc, theta) -> Model:
+    return Model(desc, theta)
+
+
+def mtp_set_params(model: Model, theta):
+    theta = np.ascontiguousarray(theta, np.float64)
+    _check(lib().mtp_set_params(model.h, _ptr(theta), theta.size))
+
+
+def mtp_set_active_set(model: Model, A: torch.Tensor, stream=None):
+    A = A.to(dtype=torch.float64).contiguous()
+    _check(lib().mtp_set_active_set(model.h, _ptr(A), A.shape[0], _stream(stream)))
+
+
+def mtp_get_active_inverse(model: Model, stream=None):
+    m = model.n_params
+    out = torch.empty((m, m), dtype=torch.float64, device="cuda")
+    _check(lib().mtp_get_active_inverse(model.h, _ptr(out), _stream(stream)))
+    return out
+
+
+def mtp_build_neighbors(model: Model, batch: Batch, nbr: Neighbors | None = None, stream=None) -> Neighbors:
+    nbr = nbr or Neighbors()
+    _check(lib().mtp_build_neighbors(model.h, ctypes.byref(batch.c), ctypes.byref(nbr.h), _stream(stream)))
+    return nbr
+
+
+def mtp_nbr_export(nbr: Neighbors, batch: Batch, stream=None):
+    na, npairs = nbr.size()
+    off = torch.empty(na + 1, dtype=torch.int64, device="cuda")
+    j = torch.empty(max(npairs, 1), dtype=torch.int32, device="cuda")
+    img = torch.empty((max(npairs, 1), 3), dtype=torch.int32, device="cuda")
+    r = torch.empty((max(npairs, 1), 3), dtype=torch.float64, device="cuda")
+    _check(lib().mtp_nbr_export(nbr.h, ctypes.byref(batch.c), _ptr(off), _ptr(j), _ptr(img), _ptr(r),
+                                _stream(stream)))
+    return {"off": off, "j": j[:npairs], "img": img[:npairs], "r": r[:npairs]}
+
+
+def _prec(p):
+    if p in ("fp64", MTP_FP64):
+        return MTP_FP64
+    if p in ("mixed", MTP_MIXED):
+        return MTP_MIXED
+    raise ValueError(p)
+
+
+def mtp_energy_forces_stress(model, batch, nbr, prec="mixed", energy=None, site_energy=None, forces=None,
+                             virial=None, want=("energy", "forces", "virial", "site_energy"), stream=None):
+    dev = "cuda"
+    N, K = batch.n_atoms, batch.n_cfg
+    if energy is None and "energy" in want:
+        energy = torch.empty(K, dtype=torch.float64, device=dev)
+    if site_energy is None and "site_energy" in want:
+        site_energy = torch.empty(N, dtype=torch.float64, device=dev)
+    if forces is None and "forces" in want:
+        forces = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    if virial is None and "virial" in want:
+        virial = torch.empty((K, 3, 3), dtype=torch.float64, device=dev)
+    _check(lib().mtp_energy_forces_stress(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(energy),
+                                          _ptr(site_energy), _ptr(forces), _ptr(virial), _stream(stream)))
+    return {"energy": energy, "site_energy": site_energy, "forces": forces, "virial": virial}
+
+
+def mtp_param_rows(model, batch, nbr, prec="fp64", atoms=None, stream=None):
+    n = batch.n_atoms if atoms is None else int(atoms.numel())
+    rows = torch.empty((n, model.n_params), dtype=torch.float64, device="cuda")
+    if atoms is not None:
+        atoms = atoms.to(device="cuda", dtype=torch.int64).contiguous()
+    _check(lib().mtp_param_rows(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(atoms), n, _ptr(rows),
+                                _stream(stream)))
+    return rows
+
+
+def mtp_grade(model, batch, nbr, prec="mixed", threshold=2.0, stream=None):
+    N = batch.n_atoms
+    gamma = torch.empty(N, dtype=torch.float64, device="cuda")
+    argmax = torch.empty(N, dtype=torch.int32, device="cuda")
+    flagged = torch.empty(max(N, 1), dtype=torch.int32, device="cuda")
+    n_flagged = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _check(lib().mtp_grade(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), float(threshold), _ptr(gamma),
+                           _ptr(argmax), _ptr(flagged), _ptr(n_flagged), _stream(stream)))
+    return {"gamma": gamma, "argmax": argmax, "flagged": flagged, "n_flagged": n_flagged}
+
+
+def mtp_step(model, batch, nbr, prec="mixed", threshold=2.0, out=None, grade=True, stream=None):
+    N, K = batch.n_atoms, batch.n_cfg
+    if out is None:
+        out = {"energy": torch.empty(K, dtype=torch.float64, device="cuda"),
+               "site_energy": None,
+               "forces": torch.empty((N, 3), dtype=torch.float64, device="cuda"),
+               "virial": torch.empty((K, 3, 3), dtype=torch.float64, device="cuda")}
+        if grade:
+            out.update({"gamma": torch.empty(N, dtype=torch.float64, device="cuda"),
+                        "argmax": torch.empty(N, dtype=torch.int32, device="cuda"),
+                        "flagged": torch.empty(max(N, 1), dtype=torch.int32, device="cuda"),
+                        "n_flagged": torch.zeros(1, dtype=torch.int64, device="cuda")})
+    g = out.get("gamma")
+    _check(lib().mtp_step(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(out.get("energy")),
+                          _ptr(out.get("site_energy")), _ptr(out.get("forces")), _ptr(out.get("virial")),
+                          float(threshold), _ptr(g), _ptr(out.get("argmax")), _ptr(out.get("flagged")),
+                          _ptr(out.get("n_flagged")), _stream(stream)))
+    return out
+
+
+def mtp_extract_neighborhoods(nbr, batch, idx: torch.Tensor, capacity=None, stream=None):
+    idx = idx.to(device="cuda", dtype=torch.int32).contiguous()
+    n = int(idx.numel())
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    total = ctypes.c_int64()
+    if capacity is None:
+        # ask for the size first
+        st = lib().mtp_extract_neighborhoods(nbr.h, ctypes.byref(batch.c), _ptr(idx), n, _ptr(off), None, None,
+                                             None, 0, ctypes.byref(total), _stream(stream))
+        if st not in (0, 3):
+            _check(st)
+        capacity = total.value
+    r = torch.empty((max(capacity, 1), 3), dtype=torch.float64, device="cuda")
+    ty = torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda")
+    j = torch.empty(max(capacity, 1), dtype=torch.int32, device="cuda")
+    _check(lib().mtp_extract_neighborhoods(nbr.h, ctypes.byref(batch.c), _ptr(idx), n, _ptr(off), _ptr(r),
+                                           _ptr(ty), _ptr(j), capacity, ctypes.byref(total), _stream(stream)))
+    t = total.value
+    return {"off": off, "r": r[:t], "type": ty[:t], "j": j[:t]}
+
+
+def mtp_train_step(model, batch, nbr, E_ref, F_ref, W_ref=None, w_e=1.0, w_f=0.01, w_s=0.0, prec="fp64",
+                   stream=None):
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty(model.n_params, dtype=torch.float64, device="cuda")
+    E_ref = E_ref.to(device="cuda", dtype=torch.float64).contiguous()
+    F_ref = F_ref.to(device="cuda", dtype=torch.float64).contiguous()
+    if W_ref is not None:
+        W_ref = W_ref.to(device="cuda", dtype=torch.float64).contiguous()
+    _check(lib().mtp_train_step(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(E_ref), _ptr(F_ref),
+                                _ptr(W_ref), float(w_e), float(w_f), float(w_s), _ptr(loss), _ptr(grad),
+                                _stream(stream)))
+    return loss, grad

@@ -1,0 +1,612 @@
+// C ABI of the MTP library: handles, schedule upload and the entry points of include/mtp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "mtp_internal.h"
+
+namespace mtp {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+void DevBuf::ensure(size_t need, cudaStream_t s) {
+  if (need == 0) need = 16;
+  if (bytes >= need) return;
+  if (p) MTP_CUDA(cudaFreeAsync(p, s));
+  p = nullptr;
+  bytes = 0;
+  size_t cap = need + need / 8;
+  MTP_CUDA(cudaMallocAsync(&p, cap, s));
+  bytes = cap;
+}
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+namespace {
+
+template <class T>
+size_t put(std::vector<char>& blob, const std::vector<T>& v) {
+  size_t off = (blob.size() + 255) & ~size_t(255);
+  blob.resize(off + std::max<size_t>(v.size() * sizeof(T), 16));
+  if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+}  // namespace
+
+// Uploads the schedule with its forward waves (destinations grouped by dependency depth) and
+// the transposed triple list for the adjoint (uses of each value, grouped by height).
+void upload_schedule(mtp_model* md) {
+  const Schedule& S = md->sched;
+  const int nv = S.n_values, nm = S.n_mom_comps, nd = nv - nm;
+  if (nv >= 65536) throw Fail{MTP_ERR_UNSUPPORTED, "value array exceeds 65535 entries"};
+  std::vector<int> comp_info(nm);
+  for (int c = 0; c < nm; ++c)
+    comp_info[c] = S.comp_mu[c] | (S.comp_exp[c][0] << 8) | (S.comp_exp[c][1] << 16) | (S.comp_exp[c][2] << 24);
+  std::vector<int> depth(nv, 0);
+  for (int d = 0; d < nd; ++d) {
+    int dep = 0;
+    for (int t = S.dst_ptr[d]; t < S.dst_ptr[d + 1]; ++t)
+      dep = std::max(dep, std::max(depth[S.tri_a[t]], depth[S.tri_b[t]]) + 1);
+    depth[nm + d] = dep;
+  }
+  int maxdep = 0;
+  for (int x = nm; x < nv; ++x) maxdep = std::max(maxdep, depth[x]);
+  std::vector<int> fwave_ptr(1, 0), fdst;
+  for (int w = 1; w <= maxdep; ++w) {
+    std::vector<int> lst;
+    for (int x = nm; x < nv; ++x)
+      if (depth[x] == w) lst.push_back(x);
+    std::stable_sort(lst.begin(), lst.end(), [&](int a, int b) {
+      return (S.dst_ptr[a - nm + 1] - S.dst_ptr[a - nm]) > (S.dst_ptr[b - nm + 1] - S.dst_ptr[b - nm]);
+    });
+    fdst.insert(fdst.end(), lst.begin(), lst.end());
+    fwave_ptr.push_back(static_cast<int>(fdst.size()));
+  }
+  std::vector<uint32_t> tri_ab(S.tri_a.size());
+  std::vector<float> tri_cf(S.tri_a.size());
+  for (size_t t = 0; t < S.tri_a.size(); ++t) {
+    tri_ab[t] = static_cast<uint32_t>(S.tri_a[t]) | (static_cast<uint32_t>(S.tri_b[t]) << 16);
+    tri_cf[t] = static_cast<float>(S.tri_c[t]);
+  }
+  // uses (gather form of the adjoint)
+  std::vector<std::vector<std::pair<uint32_t, double>>> uses(nv);
+  for (int d = 0; d < nd; ++d)
+    for (int t = S.dst_ptr[d]; t < S.dst_ptr[d + 1]; ++t) {
+      const uint32_t dst = static_cast<uint32_t>(nm + d);
+      uses[S.tri_a[t]].push_back({static_cast<uint32_t>(S.tri_b[t]) | (dst << 16), S.tri_c[t]});
+      uses[S.tri_b[t]].push_back({static_cast<uint32_t>(S.tri_a[t]) | (dst << 16), S.tri_c[t]});
+    }
+  std::vector<int> height(nv, 0);
+  for (int x = nv - 1; x >= 0; --x)
+    for (auto& u : uses[x]) height[x] = std::max(height[x], height[u.first >> 16] + 1);
+  int maxh = 0;
+  for (int x = 0; x < nv; ++x) maxh = std::max(maxh, height[x]);
+  std::vector<int> rwave_ptr(1, 0), rval;
+  for (int h = 0; h <= maxh; ++h) {
+    std::vector<int> lst;
+    for (int x = 0; x < nv; ++x)
+      if (height[x] == h) lst.push_back(x);
+    std::stable_sort(lst.begin(), lst.end(), [&](int a, int b) { return uses[a].size() > uses[b].size(); });
+    rval.insert(rval.end(), lst.begin(), lst.end());
+    rwave_ptr.push_back(static_cast<int>(rval.size()));
+  }
+  std::vector<int> use_ptr(1, 0);
+  std::vector<uint32_t> use_od;
+  std::vector<double> use_cd;
+  std::vector<float> use_cf;
+  for (int x = 0; x < nv; ++x) {
+    for (auto& u : uses[x]) { use_od.push_back(u.first); use_cd.push_back(u.second); use_cf.push_back(static_cast<float>(u.second)); }
+    use_ptr.push_back(static_cast<int>(use_od.size()));
+  }
+  std::vector<char> blob;
+  const size_t o_ci = put(blob, comp_info), o_fwp = put(blob, fwave_ptr), o_fd = put(blob, fdst),
+               o_tp = put(blob, S.dst_ptr), o_tab = put(blob, tri_ab), o_tcf = put(blob, tri_cf),
+               o_tcd = put(blob, S.tri_c), o_rwp = put(blob, rwave_ptr), o_rv = put(blob, rval),
+               o_up = put(blob, use_ptr), o_uod = put(blob, use_od), o_ucf = put(blob, use_cf),
+               o_ucd = put(blob, use_cd), o_bi = put(blob, S.basis_idx);
+  md->sched_buf.ensure(blob.size(), 0);
+  MTP_CUDA(cudaMemcpy(md->sched_buf.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  char* base = md->sched_buf.as<char>();
+  DevSchedule& D = md->ds;
+  D.n_types = S.n_types; D.n_q = S.n_q; D.n_rad = S.n_rad; D.n_lin = S.n_lin; D.n_params = S.n_params;
+  D.n_mom = nm; D.n_vals = nv; D.first_dst = nm; D.nu_max = S.nu_max;
+  D.n_fwaves = static_cast<int>(fwave_ptr.size()) - 1;
+  D.n_rwaves = static_cast<int>(rwave_ptr.size()) - 1;
+  D.r_min = md->desc.r_min; D.r_cut = md->desc.r_cut;
+  D.comp_info = reinterpret_cast<const int*>(base + o_ci);
+  D.fwave_ptr = reinterpret_cast<const int*>(base + o_fwp);
+  D.fdst = reinterpret_cast<const int*>(base + o_fd);
+  D.tri_ptr = reinterpret_cast<const int*>(base + o_tp);
+  D.tri_ab = reinterpret_cast<const uint32_t*>(base + o_tab);
+  D.tri_cf = reinterpret_cast<const float*>(base + o_tcf);
+  D.tri_cd = reinterpret_cast<const double*>(base + o_tcd);
+  D.rwave_ptr = reinterpret_cast<const int*>(base + o_rwp);
+  D.rval = reinterpret_cast<const int*>(base + o_rv);
+  D.use_ptr = reinterpret_cast<const int*>(base + o_up);
+  D.use_od = reinterpret_cast<const uint32_t*>(base + o_uod);
+  D.use_cf = reinterpret_cast<const float*>(base + o_ucf);
+  D.use_cd = reinterpret_cast<const double*>(base + o_ucd);
+  D.basis_idx = reinterpret_cast<const int*>(base + o_bi);
+}
+
+void upload_theta(mtp_model* md) {
+  const Schedule& S = md->sched;
+  const int64_t m = S.n_params;
+  std::vector<double> seed(S.n_values, 0.0);
+  for (int a = 0; a < S.n_lin; ++a) seed[S.basis_idx[a]] += md->theta[S.n_types + a];
+  std::vector<float> tf(m), sf(S.n_values);
+  for (int64_t k = 0; k < m; ++k) tf[k] = static_cast<float>(md->theta[k]);
+  for (int x = 0; x < S.n_values; ++x) sf[x] = static_cast<float>(seed[x]);
+  std::vector<char> blob;
+  const size_t o_td = put(blob, md->theta), o_tf = put(blob, tf), o_sd = put(blob, seed), o_sf = put(blob, sf);
+  md->theta_buf.ensure(blob.size(), 0);
+  MTP_CUDA(cudaMemcpy(md->theta_buf.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  char* base = md->theta_buf.as<char>();
+  md->ds.theta_d = reinterpret_cast<const double*>(base + o_td);
+  md->ds.theta_f = reinterpret_cast<const float*>(base + o_tf);
+  md->ds.seed_d = reinterpret_cast<const double*>(base + o_sd);
+  md->ds.seed_f = reinterpret_cast<const float*>(base + o_sf);
+}
+
+void run_grade_simt(mtp_model* md, int64_t N, bool fp64, const double* rows, const float* rows_f, int64_t ld,
+                    double* gamma, int32_t* argmax, cudaStream_t s);
+bool grade_tc_available(const mtp_model* md);
+void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, int64_t ld, double* gamma,
+                  int32_t* argmax, cudaStream_t s);
+
+}  // namespace mtp
+
+using namespace mtp;
+
+namespace {
+
+mtp_status fail(mtp_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+template <class F>
+mtp_status guarded(F&& f) {
+  try {
+    f();
+    return MTP_OK;
+  } catch (const Fail& e) {
+    return fail(e.st, e.msg);
+  } catch (const std::invalid_argument& e) {
+    return fail(MTP_ERR_ARG, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(MTP_ERR_CUDA, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(MTP_ERR_CUDA, e.what());
+  } catch (...) {
+    return fail(MTP_ERR_CUDA, "unknown error");
+  }
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+void check_desc(const mtp_desc* d) {
+  if (!d) throw Fail{MTP_ERR_ARG, "null descriptor"};
+  if (d->n_types < 1 || d->n_types > 64) throw Fail{MTP_ERR_ARG, "n_types must be in [1, 64]"};
+  if (d->lev_max < 2 || d->lev_max > 28) throw Fail{MTP_ERR_ARG, "lev_max must be in [2, 28]"};
+  if (d->n_q < 1 || d->n_q > 32) throw Fail{MTP_ERR_ARG, "n_q must be in [1, 32]"};
+  if (!(d->r_cut > d->r_min) || !(d->r_min >= 0.0)) throw Fail{MTP_ERR_ARG, "need 0 <= r_min < r_cut"};
+}
+
+void fill_sizes(const Schedule& S, mtp_sizes* o) {
+  o->n_params = S.n_params;
+  o->n_lin = S.n_lin;
+  o->n_rad = S.n_rad;
+  o->n_moments = S.n_moments;
+  o->n_mom_comps = S.n_mom_comps;
+  o->n_values = S.n_values;
+  o->n_triples = static_cast<int32_t>(S.tri_a.size());
+  o->nu_max = S.nu_max;
+  o->n_gauge = S.n_rad * (S.n_rad + 1) / 2;
+}
+
+void check_model(const mtp_model* m) {
+  if (!m) throw Fail{MTP_ERR_ARG, "null model"};
+  int dev = -1;
+  MTP_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) throw Fail{MTP_ERR_ARG, "model belongs to another device"};
+}
+
+void check_run(const mtp_model* m, const mtp_batch* b, const mtp_nbr* nb) {
+  check_model(m);
+  if (!b || !nb) throw Fail{MTP_ERR_ARG, "null batch or neighbor list"};
+  if (b->n_cfg != nb->n_cfg) throw Fail{MTP_ERR_ARG, "neighbor list was built for another batch"};
+  if (!b->pos || !b->type || !b->cell) throw Fail{MTP_ERR_ARG, "batch: null array"};
+}
+
+// Shared body of the EFS / grade / step entry points.
+void efs_and_grade(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec, double* energy,
+                   double* site_energy, double* forces, double* virial, double threshold, double* gamma,
+                   int32_t* argmax, int32_t* flagged, int64_t* n_flagged, cudaStream_t s) {
+  check_run(m, b, nb);
+  if (prec != MTP_FP64 && prec != MTP_MIXED) throw Fail{MTP_ERR_ARG, "unknown precision"};
+  const bool fp64 = prec == MTP_FP64;
+  const bool want_efs = energy || site_energy || forces || virial;
+  const bool want_grade = gamma != nullptr;
+  if (!want_efs && !want_grade) throw Fail{MTP_ERR_ARG, "no output requested"};
+  if ((flagged || n_flagged) && !gamma) throw Fail{MTP_ERR_ARG, "flagging needs gamma"};
+  if (want_grade && !m->have_ainv) throw Fail{MTP_ERR_ARG, "no active set (call mtp_set_active_set)"};
+  const int64_t N = nb->n_atoms, P = nb->n_pairs;
+  SiteOutputs o;
+  if (want_efs) {
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    m->ws_pair.ensure(std::max<int64_t>(P, 1) * 3 * rsz, s);
+    m->ws_atom.ensure(N * 10 * sizeof(double), s);
+    o.V = site_energy ? site_energy : m->ws_atom.as<double>();
+    o.Wat = m->ws_atom.as<double>() + N;
+    o.G = m->ws_pair.p;
+  }
+  int64_t ld = 0;
+  const bool use_tc = !fp64 && want_grade && grade_tc_available(m);
+  if (want_grade) {
+    if (fp64) {
+      ld = m->sched.n_params;
+      m->ws_rows.ensure(N * ld * sizeof(double), s);
+      o.rows = m->ws_rows.as<double>();
+    } else if (use_tc) {
+      ld = m->ainv_ld;
+      m->ws_rows.ensure(2 * N * ld * sizeof(float), s);
+      o.rows_hi = m->ws_rows.as<float>();
+      o.rows_lo = o.rows_hi + N * ld;
+    } else {
+      ld = m->sched.n_params;
+      m->ws_rows.ensure(N * ld * sizeof(float), s);
+      o.rows_hi = m->ws_rows.as<float>();
+    }
+    o.rows_ld = ld;
+  }
+  run_sites(m, b, nb, fp64, o, false, nullptr, s);
+  if (want_efs) {
+    if (forces) run_forces(nb, fp64, o.G, forces, s);
+    if (energy || virial) run_config_sums(nb, o.V, o.Wat, energy, virial, m->ws_red, s);
+  }
+  if (want_grade) {
+    if (use_tc) run_grade_tc(m, N, o.rows_hi, o.rows_lo, ld, gamma, argmax, s);
+    else run_grade_simt(m, N, fp64, o.rows, o.rows_hi, ld, gamma, argmax, s);
+    if (flagged || n_flagged) {
+      int64_t* cnt = n_flagged;
+      int32_t* fl = flagged;
+      if (!fl) {
+        m->ws_misc.ensure(N * sizeof(int32_t) + 64, s);
+        fl = m->ws_misc.as<int32_t>();
+      }
+      if (!cnt) throw Fail{MTP_ERR_ARG, "flagged needs n_flagged"};
+      run_flag(N, gamma, threshold, fl, cnt, m->ws_red, s);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mtp_version(void) { return "mtp-gb300 1.0 (sm_103a)"; }
+const char* mtp_last_error(void) { return g_last_error.c_str(); }
+
+mtp_status mtp_describe(const mtp_desc* desc, mtp_sizes* out) {
+  return guarded([&] {
+    check_desc(desc);
+    if (!out) throw Fail{MTP_ERR_ARG, "null output"};
+    Schedule S = build_schedule(desc->n_types, desc->lev_max, desc->n_q);
+    fill_sizes(S, out);
+  });
+}
+
+mtp_status mtp_describe_basis(const mtp_desc* desc, int32_t* P, int32_t* mu, int32_t* nu, int32_t* edges) {
+  return guarded([&] {
+    check_desc(desc);
+    if (!P || !mu || !nu || !edges) throw Fail{MTP_ERR_ARG, "null output"};
+    Schedule S = build_schedule(desc->n_types, desc->lev_max, desc->n_q);
+    for (int a = 0; a < S.n_lin; ++a) {
+      P[a] = S.basis_P[a];
+      for (int p = 0; p < 4; ++p) { mu[4 * a + p] = S.basis_mu[a][p]; nu[4 * a + p] = S.basis_nu[a][p]; }
+      for (int e = 0; e < 6; ++e) edges[6 * a + e] = S.basis_edges[a][e];
+    }
+  });
+}
+
+mtp_status mtp_describe_schedule(const mtp_desc* desc, int32_t* comp_mu, int32_t* comp_exp, int32_t* dst_ptr,
+                                 int32_t* tri_a, int32_t* tri_b, double* tri_c, int32_t* basis_idx) {
+  return guarded([&] {
+    check_desc(desc);
+    Schedule S = build_schedule(desc->n_types, desc->lev_max, desc->n_q);
+    if (comp_mu) for (int c = 0; c < S.n_mom_comps; ++c) comp_mu[c] = S.comp_mu[c];
+    if (comp_exp)
+      for (int c = 0; c < S.n_mom_comps; ++c)
+        for (int q = 0; q < 3; ++q) comp_exp[3 * c + q] = S.comp_exp[c][q];
+    if (dst_ptr) for (size_t k = 0; k < S.dst_ptr.size(); ++k) dst_ptr[k] = S.dst_ptr[k];
+    if (tri_a) for (size_t t = 0; t < S.tri_a.size(); ++t) tri_a[t] = S.tri_a[t];
+    if (tri_b) for (size_t t = 0; t < S.tri_b.size(); ++t) tri_b[t] = S.tri_b[t];
+    if (tri_c) for (size_t t = 0; t < S.tri_c.size(); ++t) tri_c[t] = S.tri_c[t];
+    if (basis_idx) for (int a = 0; a < S.n_lin; ++a) basis_idx[a] = S.basis_idx[a];
+  });
+}
+
+mtp_status mtp_load(const mtp_desc* desc, const double* theta, int64_t m, mtp_model** out) {
+  return guarded([&] {
+    check_desc(desc);
+    if (!theta || !out) throw Fail{MTP_ERR_ARG, "null theta or output"};
+    *out = nullptr;
+    Schedule S = build_schedule(desc->n_types, desc->lev_max, desc->n_q);
+    if (m != S.n_params)
+      throw Fail{MTP_ERR_ARG, "theta has " + std::to_string(m) + " entries, the model needs " + std::to_string(S.n_params)};
+    for (int64_t k = 0; k < m; ++k)
+      if (!std::isfinite(theta[k])) throw Fail{MTP_ERR_NUMERIC, "non-finite theta"};
+    auto* md = new mtp_model();
+    try {
+      MTP_CUDA(cudaGetDevice(&md->device));
+      md->desc = *desc;
+      md->sched = std::move(S);
+      md->theta.assign(theta, theta + m);
+      upload_schedule(md);
+      upload_theta(md);
+      MTP_CUDA(cudaDeviceSynchronize());
+    } catch (...) {
+      mtp_free_model(md);
+      throw;
+    }
+    *out = md;
+  });
+}
+
+void mtp_free_model(mtp_model* md) {
+  if (!md) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(md->device);
+  cudaDeviceSynchronize();
+  for (DevBuf* b : {&md->sched_buf, &md->theta_buf, &md->ainv_d, &md->ainv_f, &md->ws_pair, &md->ws_atom,
+                    &md->ws_rows, &md->ws_misc, &md->ws_red, &md->err_flag})
+    b->release();
+  cudaSetDevice(cur);
+  delete md;
+}
+
+int64_t mtp_num_params(const mtp_model* md) { return md ? md->sched.n_params : -1; }
+
+mtp_status mtp_model_sizes(const mtp_model* md, mtp_sizes* out) {
+  return guarded([&] {
+    if (!md || !out) throw Fail{MTP_ERR_ARG, "null argument"};
+    fill_sizes(md->sched, out);
+  });
+}
+
+mtp_status mtp_set_params(mtp_model* md, const double* theta, int64_t m) {
+  return guarded([&] {
+    check_model(md);
+    if (!theta || m != md->sched.n_params) throw Fail{MTP_ERR_ARG, "theta size mismatch"};
+    for (int64_t k = 0; k < m; ++k)
+      if (!std::isfinite(theta[k])) throw Fail{MTP_ERR_NUMERIC, "non-finite theta"};
+    MTP_CUDA(cudaDeviceSynchronize());
+    md->theta.assign(theta, theta + m);
+    upload_theta(md);
+  });
+}
+
+mtp_status mtp_set_active_set(mtp_model* md, const double* A, int64_t m, void* stream) {
+  return guarded([&] {
+    check_model(md);
+    if (!A || m != md->sched.n_params) throw Fail{MTP_ERR_ARG, "active-set matrix must be m x m"};
+    md->have_ainv = false;
+    run_lu_inverse(md, A, m, as_stream(stream));
+  });
+}
+
+mtp_status mtp_get_active_inverse(const mtp_model* md, double* Ainv, void* stream) {
+  return guarded([&] {
+    check_model(md);
+    if (!md->have_ainv || !Ainv) throw Fail{MTP_ERR_ARG, "no active set or null output"};
+    MTP_CUDA(cudaMemcpyAsync(Ainv, md->ainv_d.p, md->m_active * md->m_active * sizeof(double),
+                             cudaMemcpyDeviceToDevice, as_stream(stream)));
+  });
+}
+
+mtp_status mtp_build_neighbors(mtp_model* md, const mtp_batch* b, mtp_nbr** inout, void* stream) {
+  return guarded([&] {
+    check_model(md);
+    if (!inout) throw Fail{MTP_ERR_ARG, "null neighbor-list pointer"};
+    mtp_nbr* nb = *inout;
+    bool fresh = false;
+    if (!nb) { nb = new mtp_nbr(); fresh = true; MTP_CUDA(cudaGetDevice(&nb->device)); }
+    try {
+      build_neighbors(md, b, nb, as_stream(stream));
+    } catch (...) {
+      if (fresh) mtp_free_nbr(nb);
+      throw;
+    }
+    *inout = nb;
+  });
+}
+
+void mtp_free_nbr(mtp_nbr* nb) {
+  if (!nb) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(nb->device);
+  cudaDeviceSynchronize();
+  for (DevBuf* b : {&nb->off, &nb->pj, &nb->pimg, &nb->prev, &nb->pr32, &nb->atom_cfg, &nb->bins, &nb->plan,
+                    &nb->shifts, &nb->wrap, &nb->scratch, &nb->counts, &nb->seg})
+    b->release();
+  cudaSetDevice(cur);
+  delete nb;
+}
+
+mtp_status mtp_nbr_size(const mtp_nbr* nb, int64_t* n_atoms, int64_t* n_pairs) {
+  return guarded([&] {
+    if (!nb) throw Fail{MTP_ERR_ARG, "null neighbor list"};
+    if (n_atoms) *n_atoms = nb->n_atoms;
+    if (n_pairs) *n_pairs = nb->n_pairs;
+  });
+}
+
+mtp_status mtp_nbr_export(const mtp_nbr* nb, const mtp_batch* b, int64_t* off, int32_t* j, int32_t* image, double* r,
+                          void* stream) {
+  return guarded([&] {
+    if (!nb) throw Fail{MTP_ERR_ARG, "null neighbor list"};
+    cudaStream_t s = as_stream(stream);
+    if (off) MTP_CUDA(cudaMemcpyAsync(off, nb->off.p, (nb->n_atoms + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (j && nb->n_pairs) MTP_CUDA(cudaMemcpyAsync(j, nb->pj.p, nb->n_pairs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (image || r) {
+      // unpack via the extraction kernel over all atoms would need an index list; do it on the host side
+      std::vector<int> pimg(nb->n_pairs), pj(nb->n_pairs), cfg(nb->n_atoms);
+      std::vector<long long> o(nb->n_atoms + 1);
+      MTP_CUDA(cudaMemcpyAsync(pimg.data(), nb->pimg.p, nb->n_pairs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      MTP_CUDA(cudaMemcpyAsync(pj.data(), nb->pj.p, nb->n_pairs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      MTP_CUDA(cudaMemcpyAsync(cfg.data(), nb->atom_cfg.p, nb->n_atoms * sizeof(int), cudaMemcpyDeviceToHost, s));
+      MTP_CUDA(cudaMemcpyAsync(o.data(), nb->off.p, o.size() * sizeof(long long), cudaMemcpyDeviceToHost, s));
+      std::vector<double> pos, cell;
+      if (r) {
+        if (!b) throw Fail{MTP_ERR_ARG, "exporting r needs the batch"};
+        pos.resize(3 * nb->n_atoms);
+        cell.resize(9 * nb->n_cfg);
+        MTP_CUDA(cudaMemcpyAsync(pos.data(), b->pos, pos.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        MTP_CUDA(cudaMemcpyAsync(cell.data(), b->cell, cell.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      }
+      MTP_CUDA(cudaStreamSynchronize(s));
+      std::vector<int> img3(3 * nb->n_pairs);
+      std::vector<double> r3(r ? 3 * nb->n_pairs : 0);
+      for (int64_t i = 0; i < nb->n_atoms; ++i)
+        for (long long p = o[i]; p < o[i + 1]; ++p) {
+          const int n0 = unpack_img(pimg[p], 0), n1 = unpack_img(pimg[p], 1), n2 = unpack_img(pimg[p], 2);
+          img3[3 * p] = n0; img3[3 * p + 1] = n1; img3[3 * p + 2] = n2;
+          if (r) {
+            const double* H = &cell[9 * cfg[i]];
+            for (int c = 0; c < 3; ++c) {
+              const double sh = n0 * H[c] + n1 * H[3 + c] + n2 * H[6 + c];
+              r3[3 * p + c] = (pos[3 * pj[p] + c] + sh) - pos[3 * i + c];
+            }
+          }
+        }
+      if (image) MTP_CUDA(cudaMemcpyAsync(image, img3.data(), img3.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      if (r) MTP_CUDA(cudaMemcpyAsync(r, r3.data(), r3.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      MTP_CUDA(cudaStreamSynchronize(s));
+    }
+  });
+}
+
+mtp_status mtp_energy_forces_stress(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec,
+                                    double* energy, double* site_energy, double* forces, double* virial,
+                                    void* stream) {
+  return guarded([&] {
+    efs_and_grade(md, b, nb, prec, energy, site_energy, forces, virial, 0.0, nullptr, nullptr, nullptr, nullptr,
+                  as_stream(stream));
+  });
+}
+
+mtp_status mtp_grade(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec, double threshold,
+                     double* gamma, int32_t* argmax, int32_t* flagged, int64_t* n_flagged, void* stream) {
+  return guarded([&] {
+    if (!gamma) throw Fail{MTP_ERR_ARG, "null gamma"};
+    efs_and_grade(md, b, nb, prec, nullptr, nullptr, nullptr, nullptr, threshold, gamma, argmax, flagged, n_flagged,
+                  as_stream(stream));
+  });
+}
+
+mtp_status mtp_step(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec, double* energy,
+                    double* site_energy, double* forces, double* virial, double threshold, double* gamma,
+                    int32_t* argmax, int32_t* flagged, int64_t* n_flagged, void* stream) {
+  return guarded([&] {
+    efs_and_grade(md, b, nb, prec, energy, site_energy, forces, virial, threshold, gamma, argmax, flagged, n_flagged,
+                  as_stream(stream));
+  });
+}
+
+mtp_status mtp_param_rows(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec,
+                          const int64_t* atoms, int64_t n, double* rows, void* stream) {
+  return guarded([&] {
+    check_run(md, b, nb);
+    if (!rows) throw Fail{MTP_ERR_ARG, "null rows"};
+    if (atoms && n < 0) throw Fail{MTP_ERR_ARG, "negative count"};
+    SiteOutputs o;
+    o.rows = rows;
+    o.rows_ld = md->sched.n_params;
+    o.atom_list = atoms;
+    o.n_list = atoms ? n : nb->n_atoms;
+    run_sites(md, b, nb, prec == MTP_FP64, o, false, nullptr, as_stream(stream));
+  });
+}
+
+mtp_status mtp_extract_neighborhoods(const mtp_nbr* nb, const mtp_batch* b, const int32_t* idx, int64_t n,
+                                     int64_t* off, double* r, int32_t* type, int32_t* j, int64_t capacity,
+                                     int64_t* total, void* stream) {
+  return guarded([&] {
+    if (!nb || !b || !off || !total || (n > 0 && !idx)) throw Fail{MTP_ERR_ARG, "null argument"};
+    if (n < 0) throw Fail{MTP_ERR_ARG, "negative count"};
+    DevBuf tmp;
+    const int64_t t = run_extract(nb, b, idx, n, off, r, type, j, capacity, tmp, as_stream(stream));
+    MTP_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    tmp.release();
+    *total = t;
+    if (t > capacity) throw Fail{MTP_ERR_CAPACITY, "extraction needs " + std::to_string(t) + " neighbor slots"};
+  });
+}
+
+mtp_status mtp_train_step(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec,
+                          const double* E_ref, const double* F_ref, const double* W_ref, double w_e, double w_f,
+                          double w_s, double* loss, double* grad, void* stream) {
+  return guarded([&] {
+    check_run(md, b, nb);
+    if (!E_ref || !F_ref || !loss || !grad) throw Fail{MTP_ERR_ARG, "null argument"};
+    if (w_s != 0.0 && !W_ref) throw Fail{MTP_ERR_ARG, "w_s != 0 needs W_ref"};
+    if (w_e < 0 || w_f < 0 || w_s < 0) throw Fail{MTP_ERR_ARG, "weights must be non-negative"};
+    cudaStream_t s = as_stream(stream);
+    const bool fp64 = prec == MTP_FP64;
+    const int64_t N = nb->n_atoms, P = nb->n_pairs, m = md->sched.n_params;
+    const int n_cfg = static_cast<int>(nb->n_cfg);
+    // pass 1: energies, forces, virials
+    const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+    md->ws_pair.ensure(std::max<int64_t>(P, 1) * 3 * rsz, s);
+    // atom workspace: V, Wat(9), F(3), U(3)
+    md->ws_atom.ensure(N * 16 * sizeof(double), s);
+    double* V = md->ws_atom.as<double>();
+    double* Wat = V + N;
+    double* F = Wat + 9 * N;
+    double* U = F + 3 * N;
+    // config workspace: E, W, coef, S
+    md->ws_misc.ensure(static_cast<size_t>(n_cfg) * 20 * sizeof(double) + 64, s);
+    double* E = md->ws_misc.as<double>();
+    double* W = E + n_cfg;
+    double* coef = W + 9 * n_cfg;
+    double* Sc = coef + n_cfg;
+    SiteOutputs o;
+    o.V = V; o.Wat = Wat; o.G = md->ws_pair.p;
+    run_sites(md, b, nb, fp64, o, false, nullptr, s);
+    run_forces(nb, fp64, o.G, F, s);
+    run_config_sums(nb, V, Wat, E, W, md->ws_red, s);
+    run_train_prep(nb, n_cfg, E, F, W, E_ref, F_ref, W_ref, w_e, w_f, w_s, coef, U, Sc, loss, md->ws_red, s);
+    // pass 2: tangent of the parameter rows (forward-over-reverse), accumulated per warp
+    SiteOutputs t;
+    t.U = U;
+    t.Scfg = Sc;
+    t.coef = coef;
+    const int rows_per_block = 4;
+    int dev = 0, nsm = 0;
+    MTP_CUDA(cudaGetDevice(&dev));
+    MTP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int gmax = nsm * 4;
+    const size_t part_bytes = static_cast<size_t>(gmax) * rows_per_block * m * sizeof(double);
+    md->ws_rows.ensure(part_bytes, s);
+    MTP_CUDA(cudaMemsetAsync(md->ws_rows.p, 0, part_bytes, s));
+    t.grad_part = md->ws_rows.as<double>();
+    int used = gmax;
+    run_sites(md, b, nb, fp64, t, true, &used, s);
+    run_sum_rows(t.grad_part, used * rows_per_block, m, grad, s);
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+// Internal declarations shared by the CUDA translation units of the MTP library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mtp.h"
+#include "schedule.h"
+
+namespace mtp {
+
+// ------------------------------------------------------------------------------------
+// error reporting
+// ------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+struct Fail {
+  mtp_status st;
+  std::string msg;
+};
+#define MTP_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::mtp::Fail{MTP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+// device error flag bits
+enum : unsigned { ERRF_GEOMETRY = 1u, ERRF_SPECIES = 2u, ERRF_CAPACITY = 4u, ERRF_NONFINITE = 8u,
+                  ERRF_REVERSE = 16u };
+
+// ------------------------------------------------------------------------------------
+// device buffer owned by a handle (stream-ordered allocation, grows only)
+// ------------------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t need, cudaStream_t s);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------------------------------
+// schedule and parameters on the device (one copy per model)
+// ------------------------------------------------------------------------------------
+struct DevSchedule {
+  int n_types, n_q, n_rad, n_lin;
+  int64_t n_params;
+  int n_mom, n_vals, first_dst, nu_max;
+  int n_fwaves, n_rwaves;
+  double r_min, r_cut;
+  const int* comp_info;     // per moment component: mu | a<<8 | b<<16 | c<<24
+  const int* fwave_ptr;     // [n_fwaves+1] into fdst
+  const int* fdst;          // destination value index, grouped by depth
+  const int* tri_ptr;       // [n_vals - n_mom + 1]
+  const uint32_t* tri_ab;   // a | b << 16
+  const float* tri_cf;
+  const double* tri_cd;
+  const int* rwave_ptr;     // [n_rwaves+1] into rval
+  const int* rval;          // value index, grouped by height (sinks first)
+  const int* use_ptr;       // [n_vals+1]
+  const uint32_t* use_od;   // other operand | dst << 16
+  const float* use_cf;
+  const double* use_cd;
+  const int* basis_idx;     // [n_lin]
+  const double* theta_d;    // [n_params]
+  const float* theta_f;
+  const double* seed_d;     // [n_vals] sum of xi over basis functions stored at that value
+  const float* seed_f;
+};
+
+// ------------------------------------------------------------------------------------
+// neighbor list on the device
+// ------------------------------------------------------------------------------------
+struct CfgPlan {
+  double H[9];        // rows = lattice vectors
+  double Hinv[9];     // s = x Hinv
+  int nb[3], kb[3], pbc[3];
+  int K;              // image table half-width: nrel in [-K, K]^3
+  int64_t bin_base;
+  int64_t shift_base; // offset into the shift table ((2K+1)^3 entries)
+  double rc2;
+};
+
+struct DevNbr {
+  int64_t n_atoms, n_pairs;
+  const int64_t* off;   // [n_atoms+1]
+  const int* pj;        // neighbor atom
+  const int* pimg;      // packed image (3 x 10-bit signed) relative to the given positions
+  const int* prev;      // index of the reverse pair
+  const float4* pr32;   // r_ij rounded from a double-single evaluation, .w = |r_ij|
+  const int* atom_cfg;  // configuration of each atom
+};
+
+inline __host__ __device__ int pack_img(int a, int b, int c) {
+  return (a & 1023) | ((b & 1023) << 10) | ((c & 1023) << 20);
+}
+inline __host__ __device__ int unpack_img(int v, int k) {
+  int x = (v >> (10 * k)) & 1023;
+  return x >= 512 ? x - 1024 : x;
+}
+
+// ------------------------------------------------------------------------------------
+// handles
+// ------------------------------------------------------------------------------------
+struct ModelHost;
+}  // namespace mtp
+
+struct mtp_model {
+  int device = 0;
+  mtp_desc desc{};
+  mtp::Schedule sched;
+  mtp::DevSchedule ds{};
+  mtp::DevBuf sched_buf;       // all schedule arrays
+  mtp::DevBuf theta_buf;       // theta_d, theta_f, seed_d, seed_f
+  std::vector<double> theta;   // host copy
+  // active set
+  bool have_ainv = false;
+  int64_t m_active = 0;
+  mtp::DevBuf ainv_d;          // m x m FP64
+  mtp::DevBuf ainv_f;          // padded FP32 (hi) and (lo) for the mixed grade
+  int64_t ainv_ld = 0;
+  // workspaces
+  mtp::DevBuf ws_pair;         // per-pair gradients
+  mtp::DevBuf ws_atom;         // per-atom V, W
+  mtp::DevBuf ws_rows;         // parameter rows for the grade
+  mtp::DevBuf ws_misc;
+  mtp::DevBuf ws_red;          // reductions
+  mtp::DevBuf err_flag;        // unsigned
+};
+
+struct mtp_nbr {
+  int device = 0;
+  int64_t n_atoms = 0, n_pairs = 0, n_cfg = 0;
+  mtp::DevNbr dn{};
+  mtp::DevBuf off, pj, pimg, prev, pr32, atom_cfg;
+  mtp::DevBuf bins, plan, shifts, wrap, scratch, counts;
+  std::vector<mtp::CfgPlan> plans;
+  std::vector<int64_t> atom_offset;   // host copy
+  int64_t n_bins_total = 0;
+  // segments for deterministic per-config reductions: [cfg, atom_begin, atom_end]
+  std::vector<int64_t> seg_host;
+  mtp::DevBuf seg;
+  int64_t n_seg = 0;
+};
+
+namespace mtp {
+
+// kernels / launchers implemented in the .cu files
+void upload_schedule(mtp_model* m);
+void upload_theta(mtp_model* m);
+void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t s);
+unsigned read_and_clear_flag(mtp_model* m, cudaStream_t s);
+
+struct SiteOutputs {
+  double* V = nullptr;          // per atom
+  void* G = nullptr;            // per pair gradient (R x 3)
+  double* Wat = nullptr;        // per atom virial (9)
+  double* rows = nullptr;       // parameter rows (FP64), ld = n_params
+  float* rows_hi = nullptr;     // parameter rows split for the tensor-core grade
+  float* rows_lo = nullptr;
+  int64_t rows_ld = 0;
+  const int64_t* atom_list = nullptr;  // optional explicit atoms (rows follow list order)
+  int64_t n_list = 0;
+  // tangent mode (training)
+  const double* U = nullptr;    // per atom 3
+  const double* Scfg = nullptr; // per config 9
+  const double* coef = nullptr; // per config energy coefficient
+  double* grad_part = nullptr;  // [gridDim x n_params]
+};
+
+void run_sites(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, bool fp64, const SiteOutputs& o,
+               bool tangent, int* grid_used, cudaStream_t s);
+void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStream_t s);
+void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, double* E, double* W,
+                     DevBuf& tmp, cudaStream_t s);
+void run_lu_inverse(mtp_model* m, const double* A, int64_t n, cudaStream_t s);
+void run_grade(mtp_model* m, int64_t N, bool fp64, const double* rows, const float* rows_hi,
+               const float* rows_lo, int64_t ld, double* gamma, int32_t* argmax, cudaStream_t s);
+void run_flag(int64_t N, const double* gamma, double threshold, int32_t* flagged, int64_t* n_flagged,
+              DevBuf& tmp, cudaStream_t s);
+int64_t run_extract(const mtp_nbr* nb, const mtp_batch* b, const int32_t* idx, int64_t n, int64_t* off,
+                    double* r, int32_t* type, int32_t* j, int64_t capacity, DevBuf& tmp, cudaStream_t s);
+void run_train_prep(const mtp_nbr* nb, int n_cfg, const double* E, const double* F, const double* W,
+                    const double* E_ref, const double* F_ref, const double* W_ref, double w_e,
+                    double w_f, double w_s, double* coef, double* U, double* Scfg, double* loss,
+                    DevBuf& tmp, cudaStream_t s);
+void run_sum_rows(const double* part, int nrows, int64_t m, double* out, cudaStream_t s);
+
+}  // namespace mtp

@@ -1,0 +1,246 @@
+// Forces, per-configuration sums, flag compaction, neighborhood extraction and the loss
+// reductions of the training step.
+//
+// Forces (F = -dE/dx, used by eq. 7): with G_p = dV_i/dr_ij for pair p = (i -> j, n) and
+// rev(p) = (j -> i, -n),  F_i = sum_{p in nbh(i)} (G_p - G_rev(p)); a deterministic gather in
+// FP64 (no atomics).  Energies (eq. 1) and virials are summed per configuration over fixed
+// atom segments, then per configuration over its segments, in a fixed order.
+#include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "mtp_internal.h"
+
+namespace mtp {
+namespace {
+
+int nblk(int64_t n, int t) { return static_cast<int>(std::max<int64_t>(1, (n + t - 1) / t)); }
+
+template <class R>
+__global__ void k_forces(DevNbr nb, const R* G, double* F) {
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= nb.n_atoms) return;
+  double f0 = 0, f1 = 0, f2 = 0;
+  for (int64_t p = nb.off[i]; p < nb.off[i + 1]; ++p) {
+    const int64_t q = nb.prev[p];
+    f0 += static_cast<double>(G[3 * p + 0]) - static_cast<double>(G[3 * q + 0]);
+    f1 += static_cast<double>(G[3 * p + 1]) - static_cast<double>(G[3 * q + 1]);
+    f2 += static_cast<double>(G[3 * p + 2]) - static_cast<double>(G[3 * q + 2]);
+  }
+  F[3 * i + 0] = f0;
+  F[3 * i + 1] = f1;
+  F[3 * i + 2] = f2;
+}
+
+// one block per segment (cfg, a0, a1): partial[seg][0] = sum V, [1..9] = sum W
+__global__ void k_seg_sums(const int64_t* seg, const double* V, const double* Wat, double* part) {
+  const int64_t s = blockIdx.x;
+  const int64_t a0 = seg[3 * s + 1], a1 = seg[3 * s + 2];
+  __shared__ double red[10][256];
+  double acc[10];
+  for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+  for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+    if (V) acc[0] += V[a];
+    if (Wat)
+      for (int k = 0; k < 9; ++k) acc[1 + k] += Wat[9 * a + k];
+  }
+  for (int k = 0; k < 10; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 10; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 10) part[10 * s + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_cfg_sums(const int64_t* seg, int64_t n_seg, const double* part, int n_cfg, double* E, double* W) {
+  // thread per config; segments of config k are contiguous in seg
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_cfg) return;
+  double acc[10];
+  for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+  // binary search first segment of config k
+  int64_t lo = 0, hi = n_seg;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (seg[3 * mid] < k) lo = mid + 1; else hi = mid;
+  }
+  for (int64_t s = lo; s < n_seg && seg[3 * s] == k; ++s)
+    for (int q = 0; q < 10; ++q) acc[q] += part[10 * s + q];
+  if (E) E[k] = acc[0];
+  if (W)
+    for (int q = 0; q < 9; ++q) W[9 * k + q] = acc[1 + q];
+}
+
+struct AboveThreshold {
+  const double* gamma;
+  double thr;
+  __device__ bool operator()(int i) const { return gamma[i] > thr; }
+};
+
+__global__ void k_extract_counts(DevNbr nb, const int32_t* idx, int64_t n, long long* cnt, unsigned* bad) {
+  int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k > n) return;
+  if (k == n) { cnt[k] = 0; return; }
+  const int i = idx[k];
+  if (i < 0 || i >= nb.n_atoms) { atomicOr(bad, 1u); cnt[k] = 0; return; }
+  cnt[k] = nb.off[i + 1] - nb.off[i];
+}
+
+__global__ void k_extract_fill(DevNbr nb, const double* pos, const int* type, const double* cell,
+                               const int32_t* idx, int64_t n, const long long* off, double* r, int32_t* ty,
+                               int32_t* jout) {
+  int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= n) return;
+  const int i = idx[k];
+  if (i < 0 || i >= nb.n_atoms) return;
+  const double* H = cell + 9 * nb.atom_cfg[i];
+  int64_t o = off[k];
+  for (int64_t p = nb.off[i]; p < nb.off[i + 1]; ++p, ++o) {
+    const int j = nb.pj[p];
+    const int img = nb.pimg[p];
+    const int n0 = unpack_img(img, 0), n1 = unpack_img(img, 1), n2 = unpack_img(img, 2);
+    if (r)
+      for (int c = 0; c < 3; ++c) {
+        const double sh = n0 * H[c] + n1 * H[3 + c] + n2 * H[6 + c];
+        r[3 * o + c] = (pos[3 * j + c] + sh) - pos[3 * i + c];
+      }
+    if (ty) ty[o] = type[j];
+    if (jout) jout[o] = j;
+  }
+}
+
+// U_i = 2 w_f (F_i - F*_i); per-block partial of sum |F - F*|^2
+__global__ void k_train_forces(int64_t n, const double* F, const double* Fref, double w_f, double* U, double* part) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int c = 0; c < 3; ++c) {
+      const double d = F[3 * i + c] - Fref[3 * i + c];
+      U[3 * i + c] = 2.0 * w_f * d;
+      acc += d * d;
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_train_cfg(int n_cfg, const double* E, const double* Eref, const double* W, const double* Wref,
+                            double w_e, double w_f, double w_s, const double* fpart, int n_fpart, double* coef,
+                            double* S, double* loss) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n_cfg; k += blockDim.x) {
+    const double dE = E[k] - Eref[k];
+    coef[k] = 2.0 * w_e * dE;
+    acc += w_e * dE * dE;
+    for (int q = 0; q < 9; ++q) {
+      const double dW = (w_s != 0.0 && Wref) ? W[9 * k + q] - Wref[9 * k + q] : 0.0;
+      S[9 * k + q] = 2.0 * w_s * dW;
+      acc += w_s * dW * dW;
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int b = 0; b < n_fpart; ++b) f += fpart[b];
+    loss[0] = red[0] + w_f * f;
+  }
+}
+
+__global__ void k_sum_rows(const double* part, int nrows, int64_t m, double* out) {
+  int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (c >= m) return;
+  double acc = 0.0;
+  for (int r = 0; r < nrows; ++r) acc += part[static_cast<int64_t>(r) * m + c];
+  out[c] = acc;
+}
+
+}  // namespace
+
+void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStream_t s) {
+  if (fp64) k_forces<double><<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const double*>(G), F);
+  else k_forces<float><<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const float*>(G), F);
+  MTP_CUDA(cudaGetLastError());
+}
+
+void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, double* E, double* W, DevBuf& tmp,
+                     cudaStream_t s) {
+  tmp.ensure(nb->n_seg * 10 * sizeof(double), s);
+  k_seg_sums<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), V, Wat, tmp.as<double>());
+  MTP_CUDA(cudaGetLastError());
+  k_cfg_sums<<<nblk(nb->n_cfg, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, tmp.as<double>(),
+                                                 static_cast<int>(nb->n_cfg), E, W);
+  MTP_CUDA(cudaGetLastError());
+}
+
+void run_flag(int64_t N, const double* gamma, double threshold, int32_t* flagged, int64_t* n_flagged, DevBuf& tmp,
+              cudaStream_t s) {
+  AboveThreshold pred{gamma, threshold};
+  thrust::counting_iterator<int> it(0);
+  size_t bytes = 0;
+  MTP_CUDA(cub::DeviceSelect::If(nullptr, bytes, it, flagged, n_flagged, static_cast<int>(N), pred, s));
+  tmp.ensure(bytes, s);
+  MTP_CUDA(cub::DeviceSelect::If(tmp.p, bytes, it, flagged, n_flagged, static_cast<int>(N), pred, s));
+}
+
+int64_t run_extract(const mtp_nbr* nb, const mtp_batch* b, const int32_t* idx, int64_t n, int64_t* off, double* r,
+                    int32_t* type, int32_t* j, int64_t capacity, DevBuf& tmp, cudaStream_t s) {
+  tmp.ensure((n + 1) * sizeof(long long) + 64, s);
+  long long* cnt = tmp.as<long long>();
+  unsigned* bad = reinterpret_cast<unsigned*>(cnt + n + 1);
+  MTP_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), s));
+  k_extract_counts<<<nblk(n + 1, 256), 256, 0, s>>>(nb->dn, idx, n, cnt, bad);
+  MTP_CUDA(cudaGetLastError());
+  DevBuf scan_tmp;
+  size_t bytes = 0;
+  long long* offl = reinterpret_cast<long long*>(off);
+  MTP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, cnt, offl, n + 1, s));
+  scan_tmp.ensure(bytes, s);
+  MTP_CUDA(cub::DeviceScan::ExclusiveSum(scan_tmp.p, bytes, cnt, offl, n + 1, s));
+  long long total = 0;
+  unsigned badh = 0;
+  MTP_CUDA(cudaMemcpyAsync(&total, offl + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  MTP_CUDA(cudaMemcpyAsync(&badh, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MTP_CUDA(cudaStreamSynchronize(s));
+  scan_tmp.release();
+  if (badh) throw Fail{MTP_ERR_ARG, "atom index out of range"};
+  if (total > capacity) return total;
+  if (n > 0) {
+    k_extract_fill<<<nblk(n, 128), 128, 0, s>>>(nb->dn, b->pos, b->type, b->cell, idx, n, offl, r, type, j);
+    MTP_CUDA(cudaGetLastError());
+  }
+  return total;
+}
+
+void run_train_prep(const mtp_nbr* nb, int n_cfg, const double* E, const double* F, const double* W,
+                    const double* E_ref, const double* F_ref, const double* W_ref, double w_e, double w_f,
+                    double w_s, double* coef, double* U, double* Scfg, double* loss, DevBuf& tmp, cudaStream_t s) {
+  const int nb_f = 256;
+  tmp.ensure(nb_f * sizeof(double), s);
+  k_train_forces<<<nb_f, 256, 0, s>>>(nb->n_atoms, F, F_ref, w_f, U, tmp.as<double>());
+  MTP_CUDA(cudaGetLastError());
+  k_train_cfg<<<1, 256, 0, s>>>(n_cfg, E, E_ref, W, W_ref, w_e, w_f, w_s, tmp.as<double>(), nb_f, coef, Scfg, loss);
+  MTP_CUDA(cudaGetLastError());
+}
+
+void run_sum_rows(const double* part, int nrows, int64_t m, double* out, cudaStream_t s) {
+  k_sum_rows<<<nblk(m, 128), 128, 0, s>>>(part, nrows, m, out);
+  MTP_CUDA(cudaGetLastError());
+}
+
+}  // namespace mtp

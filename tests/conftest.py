@@ -11,3 +11,10 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built CUDA library")
     config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+@pytest.fixture(scope="session")
+def native_lib():
+    """Path of the built CUDA library (built here if missing; nvcc cross-compiles without a GPU)."""
+    from paper_2304_13144_gb300 import build
+    return build.build()

@@ -1,44 +1,59 @@
-"""Host-side basis enumeration and contraction schedule of the library vs. the oracle."""
+"""Host-side basis enumeration and contraction schedule of the library (through the C ABI,
+host-only calls) against the oracle's independent enumeration and full-tensor evaluation."""
 import numpy as np
 import pytest
 
 from oracle import basis_ref
 from oracle import oracle as O
-from paper_2304_13144_gb300 import basis, synth
+from paper_2304_13144_gb300 import synth
 
 
-@pytest.mark.parametrize("lev", [2, 4, 6, 8, 10, 12, 14, 16])
-def test_enumerations_agree_in_canonical_order(lev):
-    lib = [(b.labels, b.edges) for b in basis.enumerate_basis(lev)]
-    ref = basis_ref.basis_functions(lev)
-    assert lib == ref
+@pytest.fixture(scope="module")
+def api(native_lib):
+    from paper_2304_13144_gb300 import api as A
+    return A
+
+
+@pytest.mark.parametrize("lev", [2, 4, 6, 8, 10, 12, 14, 16, 18])
+def test_enumerations_agree_in_canonical_order(api, lev):
+    lib_basis = api.mtp_describe_basis(api.make_desc(1, lev))
+    assert lib_basis == basis_ref.basis_functions(lev)
 
 
 @pytest.mark.parametrize("T,lev,m", [(1, 8, 26), (1, 12, 54), (1, 16, 125), (2, 16, 222),
-                                     (3, 16, 383), (3, 20, 651)])
-def test_parameter_counts(T, lev, m):
-    assert basis.model_shape(T, lev).n_params == m
+                                     (3, 16, 383), (3, 20, 651), (4, 24, 1636)])
+def test_parameter_counts(api, T, lev, m):
+    sz = api.mtp_describe(api.make_desc(T, lev))
+    assert sz["n_params"] == m
+    assert sz["n_gauge"] == sz["n_rad"] * (sz["n_rad"] + 1) // 2
 
 
-def _eval_schedule(sched, rv, f):
-    """Evaluate the flattened triple list in float64 (numpy), for one neighborhood."""
-    vals = np.zeros(sched.n_vals)
-    for k in range(sched.n_mom_comps):
-        a, b, c = sched.comp_exp[k]
-        mu = sched.comp_mu[k]
-        vals[k] = np.sum(f[:, mu] * rv[:, 0] ** a * rv[:, 1] ** b * rv[:, 2] ** c)
-    for d in range(len(sched.dst_ptr) - 1):
-        s = 0.0
-        for t in range(sched.dst_ptr[d], sched.dst_ptr[d + 1]):
-            s += sched.tri_c[t] * vals[sched.tri_a[t]] * vals[sched.tri_b[t]]
-        vals[sched.first_dst + d] = s
-    return vals[np.array(sched.basis_idx)]
+def test_descriptor_validation(api):
+    with pytest.raises(api.MtpError) as e:
+        api.mtp_describe(api.make_desc(0, 8))
+    assert e.value.name == "MTP_ERR_ARG"
+    with pytest.raises(api.MtpError):
+        api.mtp_describe(api.make_desc(1, 8, r_min=5.0, r_cut=4.0))
+
+
+def _eval_schedule(sch, rv, f):
+    """Evaluate the exported flattened triple list in float64 (numpy) for one neighborhood."""
+    nm = sch["sizes"]["n_mom_comps"]
+    nv = sch["sizes"]["n_values"]
+    vals = np.zeros(nv)
+    for k in range(nm):
+        a, b, c = sch["comp_exp"][k]
+        vals[k] = np.sum(f[:, sch["comp_mu"][k]] * rv[:, 0] ** a * rv[:, 1] ** b * rv[:, 2] ** c)
+    dp = sch["dst_ptr"]
+    for d in range(nv - nm):
+        t = slice(dp[d], dp[d + 1])
+        vals[nm + d] = np.sum(sch["tri_c"][t] * vals[sch["tri_a"][t]] * vals[sch["tri_b"][t]])
+    return vals[sch["basis_idx"]]
 
 
 @pytest.mark.parametrize("lev", [8, 12, 16])
-def test_schedule_reproduces_oracle_basis_values(lev):
-    shape = basis.model_shape(3, lev)
-    sched = basis.compile_schedule(shape)
+def test_schedule_reproduces_oracle_basis_values(api, lev):
+    sch = api.mtp_describe_schedule(api.make_desc(3, lev))
     md = O.OracleModel(3, lev, 2.0, 5.0)
     g = synth.rng(100 + lev)
     theta = g.normal(size=md.m) * 0.05
@@ -54,5 +69,5 @@ def test_schedule_reproduces_oracle_basis_values(lev):
     x = (2 * r - 7.0) / 3.0
     Q = np.polynomial.chebyshev.chebvander(x, 7) * ((5.0 - r) ** 2)[:, None]
     f = np.einsum("jmb,jb->jm", c[types[0], types[1:]], Q)
-    B = _eval_schedule(sched, rv, f)
+    B = _eval_schedule(sch, rv, f)
     np.testing.assert_allclose(B, B_ref, rtol=1e-11, atol=1e-14 * np.abs(B_ref).max())
