@@ -109,6 +109,14 @@ mtp_status mtp_describe_schedule(const mtp_desc* desc, int32_t* comp_mu, int32_t
                                  int32_t* dst_ptr, int32_t* tri_a, int32_t* tri_b,
                                  double* tri_c, int32_t* basis_idx);
 
+/* Host-only: the n_gauge = n_rad (n_rad + 1) / 2 null directions of the parameter rows
+ * (rows of D, host, n_gauge x m).  V is unchanged when the radial functions are mixed
+ * lower-triangularly, f_mu -> f_mu + eps f_mu' (mu' <= mu, eq. 4), with xi compensating
+ * (eqs. 2, 5-6), so b_i . d = 0 for every neighborhood and direction d: an active set of m
+ * raw rows is always singular, and a full-rank one takes m - n_gauge rows plus these
+ * directions.  The paper does not discuss this.  Calls no CUDA API. */
+mtp_status mtp_gauge_directions(const mtp_desc* desc, const double* theta, int64_t m, double* D);
+
 /* Create a model on the current device.  theta: host, m doubles (layout above).
  * Enumerates the basis (Section II.A), compiles the contraction schedule and uploads it. */
 mtp_status mtp_load(const mtp_desc* desc, const double* theta, int64_t m, mtp_model** out);
@@ -209,6 +217,20 @@ mtp_status mtp_train_step(mtp_model* model, const mtp_batch* batch, const mtp_nb
                           mtp_precision prec, const double* E_ref, const double* F_ref,
                           const double* W_ref, double w_e, double w_f, double w_s, double* loss,
                           double* grad, void* stream);
+
+/* ---------------------------------------------------------------------------------- */
+/* Tracing (no counterpart in the paper)                                              */
+/* ---------------------------------------------------------------------------------- */
+
+/* Enable (on != 0) or disable kernel-level tracing: while enabled, every kernel region
+ * the library launches records a CUDA event pair on the stream it runs on. */
+mtp_status mtp_profiler_enable(int on);
+
+/* Synchronise the recorded events, then report per region name (in order of first
+ * appearance, at most `capacity` regions): names[48*k] (NUL-terminated), total device
+ * time ms[k] and number of launches launches[k]; *count = regions written.  Clears the
+ * record.  Host arrays; any of names/ms/launches may be NULL. */
+mtp_status mtp_profiler_read(int32_t capacity, char* names, double* ms, int64_t* launches, int32_t* count);
 
 #ifdef __cplusplus
 }

@@ -55,6 +55,7 @@ _SIGS = {
     "mtp_describe": (ctypes.c_int, [_P, _P]),
     "mtp_describe_basis": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "mtp_describe_schedule": (ctypes.c_int, [_P] * 8),
+    "mtp_gauge_directions": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mtp_load": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mtp_free_model": (None, [_P]),
     "mtp_num_params": (_I64, [_P]),
@@ -72,6 +73,8 @@ _SIGS = {
     "mtp_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _D, _P, _P, _P, _P, _P]),
     "mtp_extract_neighborhoods": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _I64, _P, _P]),
     "mtp_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _P, _P, _P]),
+    "mtp_profiler_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mtp_profiler_read": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -158,6 +161,14 @@ def mtp_describe_schedule(desc) -> dict:
                                                               "tri_c", "basis_idx")]))
     out["sizes"] = sz
     return out
+
+
+def mtp_gauge_directions(desc, theta):
+    theta = np.ascontiguousarray(theta, np.float64)
+    sz = mtp_describe(desc)
+    D = np.zeros((sz["n_gauge"], sz["n_params"]))
+    _check(lib().mtp_gauge_directions(ctypes.byref(desc), _ptr(theta), theta.size, _ptr(D)))
+    return D
 
 
 # ------------------------------------------------------------------------------------
@@ -367,3 +378,22 @@ def mtp_train_step(model, batch, nbr, E_ref, F_ref, W_ref=None, w_e=1.0, w_f=0.0
                                 _ptr(W_ref), float(w_e), float(w_f), float(w_s), _ptr(loss), _ptr(grad),
                                 _stream(stream)))
     return loss, grad
+
+
+def mtp_profiler_enable(on=True):
+    _check(lib().mtp_profiler_enable(1 if on else 0))
+
+
+def mtp_profiler_read(capacity=64):
+    """{region: (total_ms, launches)} since the last read (synchronises the recorded events)."""
+    names = ctypes.create_string_buffer(48 * capacity)
+    ms = np.zeros(capacity)
+    launches = np.zeros(capacity, np.int64)
+    cnt = ctypes.c_int32()
+    _check(lib().mtp_profiler_read(capacity, names, _ptr(ms), _ptr(launches), ctypes.byref(cnt)))
+    raw = names.raw
+    out = {}
+    for k in range(cnt.value):
+        nm = raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[k]), int(launches[k]))
+    return out

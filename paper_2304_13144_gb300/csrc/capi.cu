@@ -337,6 +337,16 @@ mtp_status mtp_describe_schedule(const mtp_desc* desc, int32_t* comp_mu, int32_t
   });
 }
 
+mtp_status mtp_gauge_directions(const mtp_desc* desc, const double* theta, int64_t m, double* D) {
+  return guarded([&] {
+    check_desc(desc);
+    if (!theta || !D) throw Fail{MTP_ERR_ARG, "null argument"};
+    Schedule S = build_schedule(desc->n_types, desc->lev_max, desc->n_q);
+    if (m != S.n_params) throw Fail{MTP_ERR_ARG, "theta size mismatch"};
+    gauge_directions(S, theta, D);
+  });
+}
+
 mtp_status mtp_load(const mtp_desc* desc, const double* theta, int64_t m, mtp_model** out) {
   return guarded([&] {
     check_desc(desc);

@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "mtp_internal.h"
+#include "profiler.h"
 
 namespace mtp {
 namespace {
@@ -198,6 +199,7 @@ void run_lu_inverse(mtp_model* md, const double* A, int64_t m, cudaStream_t s) {
   md->ws_misc.ensure(sizeof(double), s);
   MTP_CUDA(cudaMemsetAsync(md->err_flag.p, 0, sizeof(unsigned), s));
   MTP_CUDA(cudaMemcpyAsync(LU, A, m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  ProfRegion pr("active_set_lu_inverse", s);
   k_maxabs<<<1, 1024, 0, s>>>(A, m * m, md->ws_misc.as<double>());
   for (int64_t k = 0; k < m; ++k) {
     k_pivot<<<1, 1024, 0, s>>>(LU, m, k, piv, md->ws_misc.as<double>(), md->err_flag.as<unsigned>());
@@ -234,6 +236,7 @@ void run_grade_simt(mtp_model* md, int64_t N, bool fp64, const double* rows, con
   const int64_t m = md->m_active;
   const unsigned g = static_cast<unsigned>((N + 63) / 64);
   if (N == 0) return;
+  ProfRegion pr(fp64 ? "grade_simt_fp64" : "grade_simt_fp32", s);
   if (fp64) k_grade_simt<double><<<g, 256, 0, s>>>(rows, ld, md->ainv_d.as<double>(), m, N, gamma, argmax);
   else k_grade_simt<float><<<g, 256, 0, s>>>(rows_f, ld, md->ainv_f.as<float>() + 2 * md->ainv_ld * md->ainv_ld, m, N,
                                              gamma, argmax);

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "mtp_internal.h"
+#include "profiler.h"
 
 namespace mtp {
 namespace {
@@ -400,6 +401,7 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.off = nb->off.as<long long>();
   A.err = m->err_flag.as<unsigned>();
   const int TB = 256;
+  ProfRegion* pr1 = new ProfRegion("neighbors_bin_count", s);
   k_prep<<<blocks_for(N, TB), TB, 0, s>>>(A);
   MTP_CUDA(cudaGetLastError());
   // bin_count has bins+1 entries (last = 0) -> bin_start[bins] = N
@@ -418,6 +420,7 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   k_pairs<false><<<blocks_for(N, 128), 128, 0, s>>>(A);
   MTP_CUDA(cudaGetLastError());
   scan_exclusive<long long>(nb->counts.as<long long>(), nb->off.as<long long>(), N + 1, nb->scratch, s);
+  delete pr1;
   long long total = 0;
   unsigned flag = 0;
   MTP_CUDA(cudaMemcpyAsync(&total, nb->off.as<long long>() + N, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -437,12 +440,14 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.pimg = nb->pimg.as<int>();
   A.pr32 = nb->pr32.as<float4>();
   A.prev = nb->prev.as<int>();
+  ProfRegion* pr2 = new ProfRegion("neighbors_fill_reverse", s);
   k_pairs<true><<<blocks_for(N, 128), 128, 0, s>>>(A);
   MTP_CUDA(cudaGetLastError());
   if (total > 0) {
     k_reverse<<<blocks_for(total, 256), 256, 0, s>>>(A, total);
     MTP_CUDA(cudaGetLastError());
   }
+  delete pr2;
   MTP_CUDA(cudaMemcpyAsync(&flag, m->err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MTP_CUDA(cudaStreamSynchronize(s));
   if (flag & ERRF_GEOMETRY) throw Fail{MTP_ERR_GEOMETRY, "coincident atoms (|r_ij| < 1e-8 A)"};

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "mtp_internal.h"
+#include "profiler.h"
 
 namespace mtp {
 namespace {
@@ -173,6 +174,7 @@ __global__ void k_sum_rows(const double* part, int nrows, int64_t m, double* out
 }  // namespace
 
 void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStream_t s) {
+  ProfRegion pr("force_gather", s);
   if (fp64) k_forces<double><<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const double*>(G), F);
   else k_forces<float><<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const float*>(G), F);
   MTP_CUDA(cudaGetLastError());
@@ -181,6 +183,7 @@ void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStre
 void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, double* E, double* W, DevBuf& tmp,
                      cudaStream_t s) {
   tmp.ensure(nb->n_seg * 10 * sizeof(double), s);
+  ProfRegion pr("config_sums", s);
   k_seg_sums<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), V, Wat, tmp.as<double>());
   MTP_CUDA(cudaGetLastError());
   k_cfg_sums<<<nblk(nb->n_cfg, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, tmp.as<double>(),
@@ -191,6 +194,7 @@ void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, doub
 void run_flag(int64_t N, const double* gamma, double threshold, int32_t* flagged, int64_t* n_flagged, DevBuf& tmp,
               cudaStream_t s) {
   AboveThreshold pred{gamma, threshold};
+  ProfRegion pr("flag_compact", s);
   thrust::counting_iterator<int> it(0);
   size_t bytes = 0;
   MTP_CUDA(cub::DeviceSelect::If(nullptr, bytes, it, flagged, n_flagged, static_cast<int>(N), pred, s));
@@ -232,6 +236,7 @@ void run_train_prep(const mtp_nbr* nb, int n_cfg, const double* E, const double*
                     double w_s, double* coef, double* U, double* Scfg, double* loss, DevBuf& tmp, cudaStream_t s) {
   const int nb_f = 256;
   tmp.ensure(nb_f * sizeof(double), s);
+  ProfRegion pr("train_residuals", s);
   k_train_forces<<<nb_f, 256, 0, s>>>(nb->n_atoms, F, F_ref, w_f, U, tmp.as<double>());
   MTP_CUDA(cudaGetLastError());
   k_train_cfg<<<1, 256, 0, s>>>(n_cfg, E, E_ref, W, W_ref, w_e, w_f, w_s, tmp.as<double>(), nb_f, coef, Scfg, loss);
@@ -239,6 +244,7 @@ void run_train_prep(const mtp_nbr* nb, int n_cfg, const double* E, const double*
 }
 
 void run_sum_rows(const double* part, int nrows, int64_t m, double* out, cudaStream_t s) {
+  ProfRegion pr("train_grad_sum", s);
   k_sum_rows<<<nblk(m, 128), 128, 0, s>>>(part, nrows, m, out);
   MTP_CUDA(cudaGetLastError());
 }

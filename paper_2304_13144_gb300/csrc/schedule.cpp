@@ -377,4 +377,64 @@ Schedule build_schedule(int n_types, int lev_max, int n_q) {
   return S;
 }
 
+// Null directions of the parameter rows.  Mixing the radial functions, f_mu -> f_mu + eps f_mu'
+// (mu' <= mu, i.e. c[.][.][mu][.] += eps c[.][.][mu'][.], eq. 4), turns to first order every
+// basis function with a factor M_{mu,nu} into itself plus eps times the function with that
+// factor relabelled M_{mu',nu}, which has a lower level and so is again a basis function
+// (eqs. 5-6).  Moving eps xi_a onto that function leaves V unchanged, so the derivative of
+// theta along this change is orthogonal to every parameter row b_i = dV_i/dtheta.
+// D: n_rad (n_rad + 1) / 2 rows of n_params, ordered by (mu, mu').
+void gauge_directions(const Schedule& S, const double* theta, double* D) {
+  const int T = S.n_types, NR = S.n_rad, NQ = S.n_q, NL = S.n_lin;
+  std::map<std::pair<std::vector<Label>, std::vector<int>>, int> index;
+  std::vector<std::vector<Label>> labels(NL);
+  std::vector<std::vector<std::vector<int>>> mats(NL);
+  for (int a = 0; a < NL; ++a) {
+    const int P = S.basis_P[a];
+    for (int p = 0; p < P; ++p) labels[a].push_back({S.basis_mu[a][p], S.basis_nu[a][p]});
+    mats[a].assign(P, std::vector<int>(P, 0));
+    std::vector<int> ev;
+    for (int i = 0; i < P; ++i)
+      for (int j = i + 1; j < P; ++j) {
+        int e6 = 0;
+        for (int t = 0; t < 6; ++t) if (kPairP[t] == i && kPairQ[t] == j) e6 = t;
+        mats[a][i][j] = mats[a][j][i] = S.basis_edges[a][e6];
+        ev.push_back(S.basis_edges[a][e6]);
+      }
+    index[{labels[a], ev}] = a;
+  }
+  const int64_t m = S.n_params;
+  int row = 0;
+  for (int mu = 0; mu < NR; ++mu)
+    for (int mu2 = 0; mu2 <= mu; ++mu2, ++row) {
+      double* d = D + static_cast<int64_t>(row) * m;
+      for (int64_t k = 0; k < m; ++k) d[k] = 0.0;
+      for (int zi = 0; zi < T; ++zi)
+        for (int zj = 0; zj < T; ++zj)
+          for (int b = 0; b < NQ; ++b) {
+            const int64_t base = T + NL + ((static_cast<int64_t>(zi) * T + zj) * NR) * NQ;
+            d[base + mu * NQ + b] = theta[base + mu2 * NQ + b];
+          }
+      for (int a = 0; a < NL; ++a) {
+        const int P = S.basis_P[a];
+        for (int p = 0; p < P; ++p) {
+          if (labels[a][p].first != mu) continue;
+          std::vector<Label> nl = labels[a];
+          nl[p].first = mu2;
+          std::vector<int> order(P);
+          for (int k = 0; k < P; ++k) order[k] = k;
+          std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nl[x] < nl[y]; });
+          std::vector<Label> sl;
+          for (int k : order) sl.push_back(nl[k]);
+          std::vector<int> ev;
+          for (int i = 0; i < P; ++i)
+            for (int j = i + 1; j < P; ++j) ev.push_back(mats[a][order[i]][order[j]]);
+          auto it = index.find({sl, canonical_edges(sl, ev)});
+          if (it == index.end()) throw std::logic_error("relabelled basis function not in the basis");
+          d[T + it->second] -= theta[T + a];
+        }
+      }
+    }
+}
+
 }  // namespace mtp

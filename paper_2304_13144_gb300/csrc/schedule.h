@@ -30,4 +30,7 @@ struct Schedule {
 // Throws std::invalid_argument on a descriptor outside the supported range.
 Schedule build_schedule(int n_types, int lev_max, int n_q);
 
+// n_rad (n_rad + 1) / 2 null directions of the parameter rows for parameters theta (rows of D).
+void gauge_directions(const Schedule& S, const double* theta, double* D);
+
 }  // namespace mtp

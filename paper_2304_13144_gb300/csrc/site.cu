@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "mtp_internal.h"
+#include "profiler.h"
 
 namespace mtp {
 namespace {
@@ -466,6 +467,8 @@ void launch_sites(const SiteParams& P0, int* grid_used, cudaStream_t s) {
     *grid_used = grid;
   }
   if (P.n_work == 0) return;
+  const char* name = (MODE & M_TAN) ? "site_tangent" : (MODE & M_EFS) ? ((MODE & M_ROWS) ? "site_efs_rows" : "site_efs") : "site_rows";
+  ProfRegion pr(name, s);
   kern<<<grid, kWarps * 32, P.L.total, s>>>(P);
   MTP_CUDA(cudaGetLastError());
 }

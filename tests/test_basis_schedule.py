@@ -71,3 +71,11 @@ def test_schedule_reproduces_oracle_basis_values(api, lev):
     f = np.einsum("jmb,jb->jm", c[types[0], types[1:]], Q)
     B = _eval_schedule(sch, rv, f)
     np.testing.assert_allclose(B, B_ref, rtol=1e-11, atol=1e-14 * np.abs(B_ref).max())
+
+
+@pytest.mark.parametrize("T,lev", [(1, 8), (3, 12), (2, 16)])
+def test_gauge_directions_match_oracle(api, T, lev):
+    md = O.OracleModel(T, lev, 2.0, 5.0)
+    theta = synth.rng(lev).normal(size=md.m)
+    np.testing.assert_array_equal(api.mtp_gauge_directions(api.make_desc(T, lev), theta),
+                                  O.gauge_directions(md, theta))

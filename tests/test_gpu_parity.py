@@ -197,12 +197,17 @@ def test_grade_is_one_on_active_set_and_flags(api):
     b = api.Batch(bnp)
     nb = api.mtp_build_neighbors(model, b)
     api.mtp_set_active_set(model, torch.tensor(A, device="cuda"))
+    ref_g, _ = O.grade(A, rows)
+    # The mixed path forms b_i in FP32: rounding the exact rows to FP32 alone moves gamma by
+    # this much for this (ill-conditioned, kappa ~ 1e7) active set; the gate allows 4x that.
+    floor = np.abs(O.grade(A, rows.astype(np.float32).astype(np.float64))[0] - ref_g)
     for prec in ("fp64", "mixed"):
         out = api.mtp_grade(model, b, nb, prec, threshold=2.0)
         g = out["gamma"].cpu().numpy()
-        tol = 1e-8 if prec == "fp64" else 1e-4
-        np.testing.assert_allclose(g[pick], 1.0, atol=tol)
-        ref_g, _ = O.grade(A, rows)
+        if prec == "fp64":
+            np.testing.assert_allclose(g[pick], 1.0, atol=1e-8)
+        else:
+            assert np.all(np.abs(g - ref_g) <= 1e-4 * np.maximum(1, ref_g) + 4 * floor.max())
         nf = int(out["n_flagged"].item())
         flagged = out["flagged"].cpu().numpy()[:nf]
         want = np.nonzero(ref_g > 2.0)[0]
