@@ -108,7 +108,22 @@ void upload_schedule(mtp_model* md) {
     for (auto& u : uses[x]) { use_od.push_back(u.first); use_cd.push_back(u.second); use_cf.push_back(static_cast<float>(u.second)); }
     use_ptr.push_back(static_cast<int>(use_od.size()));
   }
+  // packed words for the specialised kernel
+  std::vector<double> coefs(S.tri_c.begin(), S.tri_c.end());
+  std::sort(coefs.begin(), coefs.end());
+  coefs.erase(std::unique(coefs.begin(), coefs.end()), coefs.end());
+  const bool packable = nv <= 4096 && coefs.size() <= 256;
+  std::vector<uint32_t> tri_pk, use_pk;
+  std::vector<float> coef_f(coefs.begin(), coefs.end());
+  if (packable) {
+    auto ci = [&](double c) { return static_cast<uint32_t>(std::lower_bound(coefs.begin(), coefs.end(), c) - coefs.begin()); };
+    for (size_t t = 0; t < S.tri_a.size(); ++t)
+      tri_pk.push_back(static_cast<uint32_t>(S.tri_a[t]) | (static_cast<uint32_t>(S.tri_b[t]) << 12) | (ci(S.tri_c[t]) << 24));
+    for (size_t u = 0; u < use_od.size(); ++u)
+      use_pk.push_back((use_od[u] & 0xffffu) | ((use_od[u] >> 16) << 12) | (ci(use_cd[u]) << 24));
+  }
   std::vector<char> blob;
+  const size_t o_tpk = put(blob, tri_pk), o_upk = put(blob, use_pk), o_cf = put(blob, coef_f);
   const size_t o_ci = put(blob, comp_info), o_fwp = put(blob, fwave_ptr), o_fd = put(blob, fdst),
                o_tp = put(blob, S.dst_ptr), o_tab = put(blob, tri_ab), o_tcf = put(blob, tri_cf),
                o_tcd = put(blob, S.tri_c), o_rwp = put(blob, rwave_ptr), o_rv = put(blob, rval),
@@ -137,6 +152,10 @@ void upload_schedule(mtp_model* md) {
   D.use_cf = reinterpret_cast<const float*>(base + o_ucf);
   D.use_cd = reinterpret_cast<const double*>(base + o_ucd);
   D.basis_idx = reinterpret_cast<const int*>(base + o_bi);
+  D.tri_pk = packable ? reinterpret_cast<const uint32_t*>(base + o_tpk) : nullptr;
+  D.use_pk = packable ? reinterpret_cast<const uint32_t*>(base + o_upk) : nullptr;
+  D.coef_f = reinterpret_cast<const float*>(base + o_cf);
+  D.n_coef = static_cast<int>(coef_f.size());
 }
 
 void upload_theta(mtp_model* md) {

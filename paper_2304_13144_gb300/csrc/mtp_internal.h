@@ -65,6 +65,12 @@ struct DevSchedule {
   const float* use_cf;
   const double* use_cd;
   const int* basis_idx;     // [n_lin]
+  // packed copies for the specialised mixed-path kernel (nullptr when n_vals > 4096 or more
+  // than 256 distinct coefficients): a | b << 12 | coef_index << 24, other | dst << 12 | ci << 24
+  const uint32_t* tri_pk;
+  const uint32_t* use_pk;
+  const float* coef_f;
+  int n_coef;
   const double* theta_d;    // [n_params]
   const float* theta_f;
   const double* seed_d;     // [n_vals] sum of xi over basis functions stored at that value
@@ -129,6 +135,7 @@ struct mtp_model {
   mtp::DevBuf ws_misc;
   mtp::DevBuf ws_red;          // reductions
   mtp::DevBuf err_flag;        // unsigned
+  bool force_generic = false;  // route the mixed path through the generic kernel (cross-checks)
 };
 
 struct mtp_nbr {

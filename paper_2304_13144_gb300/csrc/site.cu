@@ -483,8 +483,11 @@ int site_max_grid(mtp_model* m, bool fp64, bool tangent) {
   return nsm * 8;
 }
 
+bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const SiteOutputs& o, cudaStream_t s);
+
 void run_sites(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, bool fp64, const SiteOutputs& o,
                bool tangent, int* grid_used, cudaStream_t s) {
+  if (!fp64 && !tangent && !m->force_generic && run_sites_fast(m, b, nb, o, s)) return;
   SiteParams P{};
   P.d = m->ds;
   P.nb = nb->dn;

@@ -1,0 +1,505 @@
+// Register-resident per-neighborhood kernel for the mixed path (FP32 arithmetic, FP64 sums).
+//
+// Same method as site.cu (eqs. 2-4, 5-6, 9 and the hand-written adjoint) specialised on the
+// shape of the moment set: at every level the moments of radial index mu are M_{mu,nu} for
+// all nu <= nu_max(mu) = max(nu_0 - 2 mu, 0), so the components of mu are exactly the
+// monomials x^a y^b z^c of degree <= nu_max(mu).  With N_rad and nu_0 as template parameters
+// every monomial index is a compile-time constant and a pair's monomials live in registers:
+//   * moments (lane = pair): per 32-component chunk each lane forms f_mu(r) x^a y^b z^c for its
+//     pair; a warp transpose-reduction leaves lane l with the sum over the 32 pairs of
+//     component l, accumulated into the neighborhood's value array in shared memory;
+//   * contraction and its adjoint: the flattened triple list, packed to one 32-bit word per
+//     term (12-bit operands, 8-bit index into a coefficient table in shared memory);
+//   * pair adjoint (lane = pair): dV/dr_ij from the broadcast dV/dM, monomials regenerated in
+//     registers, gradient of every monomial from its lower-degree neighbours.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <utility>
+
+#include "mtp_internal.h"
+#include "profiler.h"
+
+namespace mtp {
+namespace {
+
+constexpr int nmono_upto(int d) { return d < 0 ? 0 : (d + 1) * (d + 2) * (d + 3) / 6; }
+constexpr int mono_index(int a, int b, int c) {
+  return nmono_upto(a + b + c - 1) + (b + c) * (b + c + 1) / 2 + c;
+}
+
+template <int NR, int NU0>
+struct Shape {
+  static constexpr int numax(int mu) { return NU0 - 2 * mu > 0 ? NU0 - 2 * mu : 0; }
+  static constexpr int NMONO = nmono_upto(NU0);
+  static constexpr int comp_base(int mu) {
+    int s = 0;
+    for (int m = 0; m < mu; ++m) s += nmono_upto(numax(m));
+    return s;
+  }
+  static constexpr int NCOMP = comp_base(NR);
+  static constexpr int NCHUNK = (NCOMP + 31) / 32;
+};
+
+template <int N>
+struct MonoTab {
+  int a[N], b[N], c[N], deg[N], parent[N], axis[N], lx[N], ly[N], lz[N];
+};
+
+template <int NU0>
+constexpr MonoTab<nmono_upto(NU0)> make_mono() {
+  MonoTab<nmono_upto(NU0)> t{};
+  int k = 0;
+  for (int d = 0; d <= NU0; ++d)
+    for (int a = d; a >= 0; --a)
+      for (int b = d - a; b >= 0; --b) {
+        const int c = d - a - b;
+        t.a[k] = a; t.b[k] = b; t.c[k] = c; t.deg[k] = d;
+        t.lx[k] = a > 0 ? mono_index(a - 1, b, c) : -1;
+        t.ly[k] = b > 0 ? mono_index(a, b - 1, c) : -1;
+        t.lz[k] = c > 0 ? mono_index(a, b, c - 1) : -1;
+        if (a > 0) { t.parent[k] = t.lx[k]; t.axis[k] = 0; }
+        else if (b > 0) { t.parent[k] = t.ly[k]; t.axis[k] = 1; }
+        else if (c > 0) { t.parent[k] = t.lz[k]; t.axis[k] = 2; }
+        else { t.parent[k] = -1; t.axis[k] = -1; }
+        ++k;
+      }
+  return t;
+}
+
+// slots of the moment pass: (monomial k, mu) in monomial-major order; first = first slot of k
+template <int N>
+struct SlotTab {
+  int k[N], mu[N], comp[N], first[N];
+};
+
+template <int NR, int NU0>
+constexpr SlotTab<Shape<NR, NU0>::NCOMP> make_slots() {
+  using Sh = Shape<NR, NU0>;
+  SlotTab<Sh::NCOMP> t{};
+  constexpr auto M = make_mono<NU0>();
+  int s = 0;
+  for (int k = 0; k < Sh::NMONO; ++k) {
+    bool first = true;
+    for (int mu = 0; mu < NR; ++mu)
+      if (M.deg[k] <= Sh::numax(mu)) {
+        t.k[s] = k; t.mu[s] = mu; t.comp[s] = Sh::comp_base(mu) + k; t.first[s] = first ? 1 : 0;
+        first = false;
+        ++s;
+      }
+  }
+  return t;
+}
+
+template <int NR, int NU0>
+struct Tab {
+  static constexpr MonoTab<nmono_upto(NU0)> mono = make_mono<NU0>();
+  static constexpr SlotTab<Shape<NR, NU0>::NCOMP> slots = make_slots<NR, NU0>();
+};
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+__device__ __forceinline__ float axis_val(int ax, float x, float y, float z) { return ax == 0 ? x : (ax == 1 ? y : z); }
+
+// v[0..31] on every lane -> on lane l, v[0] = sum over lanes of the original v[l].
+__device__ __forceinline__ void transpose_reduce(float (&v)[32], int lane) {
+  static_for<0, 5>([&](auto S) {
+    constexpr int s = 16 >> decltype(S)::value;
+    const bool up = (lane & s) != 0;
+    static_for<0, s>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    });
+  });
+}
+
+struct FastParams {
+  DevSchedule d;
+  DevNbr nb;
+  const int* type;
+  int64_t n_work;
+  SiteOutputs o;
+  int NQ, CBN, NC, NV;
+  size_t c_bytes, tab_bytes, warp_bytes, total;
+};
+
+// radial functions f_mu, f'_mu (eq. 4) for one pair; Q_b written to Qrow if given
+template <int NR>
+__device__ __forceinline__ void radial(float rr, const float* cz, int NQ, float rmin, float rcut, float (&f)[NR],
+                                       float (&df)[NR], float* Qrow) {
+  const float x = (2.f * rr - (rmin + rcut)) * (1.f / (rcut - rmin));
+  const float w = rcut - rr;
+  const float w2 = w * w;
+  const float dxdr = 2.f / (rcut - rmin);
+  float t0 = 1.f, t1 = x, d0 = 0.f, d1 = 1.f;
+#pragma unroll
+  for (int mu = 0; mu < NR; ++mu) { f[mu] = 0.f; df[mu] = 0.f; }
+  for (int b = 0; b < NQ; ++b) {
+    float tb, db;
+    if (b == 0) { tb = t0; db = d0; }
+    else if (b == 1) { tb = t1; db = d1; }
+    else {
+      const float t2 = 2.f * x * t1 - t0;
+      const float d2 = 2.f * t1 + 2.f * x * d1 - d0;
+      t0 = t1; t1 = t2; d0 = d1; d1 = d2;
+      tb = t2; db = d2;
+    }
+    const float q = tb * w2;
+    const float dq = db * dxdr * w2 - 2.f * tb * w;
+    if (Qrow) Qrow[b] = q;
+#pragma unroll
+    for (int mu = 0; mu < NR; ++mu) {
+      const float c = cz[mu * NQ + b];
+      f[mu] = fmaf(c, q, f[mu]);
+      df[mu] = fmaf(c, dq, df[mu]);
+    }
+  }
+}
+
+template <int NR, int NU0>
+__device__ __forceinline__ void moments_pass(float rx, float ry, float rz, const float (&f)[NR], float* vals,
+                                             const int* slot_comp, int lane) {
+  using Sh = Shape<NR, NU0>;
+  using Tb = Tab<NR, NU0>;
+  float mono[Sh::NMONO];
+  static_for<0, Sh::NCHUNK>([&](auto C) {
+    constexpr int c = decltype(C)::value;
+    float v[32];
+    static_for<0, 32>([&](auto Tt) {
+      constexpr int t = decltype(Tt)::value;
+      constexpr int s = 32 * c + t;
+      if constexpr (s < Sh::NCOMP) {
+        constexpr int k = Tb::slots.k[s];
+        constexpr int mu = Tb::slots.mu[s];
+        constexpr int first = Tb::slots.first[s];
+        if constexpr (first != 0) {
+          if constexpr (k == 0) {
+            mono[0] = 1.f;
+          } else {
+            constexpr int par = Tb::mono.parent[k];
+            constexpr int ax = Tb::mono.axis[k];
+            mono[k] = mono[par] * axis_val(ax, rx, ry, rz);
+          }
+        }
+        v[t] = f[mu] * mono[k];
+      } else {
+        v[t] = 0.f;
+      }
+    });
+    transpose_reduce(v, lane);
+    const int s = 32 * c + lane;
+    if (s < Sh::NCOMP) vals[slot_comp[s]] += v[0];
+  });
+}
+
+template <int NR, int NU0>
+__device__ __forceinline__ void adjoint_pass(float rx, float ry, float rz, const float (&f)[NR], const float* grads,
+                                             float (&g)[NR], float& gx, float& gy, float& gz) {
+  using Sh = Shape<NR, NU0>;
+  using Tb = Tab<NR, NU0>;
+  float mono[Sh::NMONO];
+  static_for<0, Sh::NMONO>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    if constexpr (k == 0) {
+      mono[0] = 1.f;
+    } else {
+      constexpr int par = Tb::mono.parent[k];
+      constexpr int ax = Tb::mono.axis[k];
+      mono[k] = mono[par] * axis_val(ax, rx, ry, rz);
+    }
+    float h = 0.f;
+    static_for<0, NR>([&](auto MU) {
+      constexpr int mu = decltype(MU)::value;
+      constexpr int dk = Tb::mono.deg[k];
+      if constexpr (dk <= Sh::numax(mu)) {
+        const float G = grads[Sh::comp_base(mu) + k];
+        g[mu] = fmaf(G, mono[k], g[mu]);
+        h = fmaf(G, f[mu], h);
+      }
+    });
+    constexpr int ea = Tb::mono.a[k], eb = Tb::mono.b[k], ec = Tb::mono.c[k];
+    constexpr int lx = Tb::mono.lx[k], ly = Tb::mono.ly[k], lz = Tb::mono.lz[k];
+    if constexpr (ea > 0) gx = fmaf(h * static_cast<float>(ea), mono[lx], gx);
+    if constexpr (eb > 0) gy = fmaf(h * static_cast<float>(eb), mono[ly], gy);
+    if constexpr (ec > 0) gz = fmaf(h * static_cast<float>(ec), mono[lz], gz);
+    // fence per degree: keeps the broadcast loads of dV/dM from being hoisted wholesale
+    if constexpr (k + 1 == nmono_upto(Tb::mono.deg[k])) __syncwarp();
+  });
+}
+
+constexpr int kWarpsF = 4;
+enum : int { F_EFS = 1, F_ROWS = 2 };
+
+template <int NR, int NU0, int MODE>
+__global__ void __launch_bounds__(kWarpsF * 32, 3) site_fast_kernel(FastParams P) {
+  using Sh = Shape<NR, NU0>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DevSchedule& d = P.d;
+  const int NQ = P.NQ, CBN = P.CBN, NV = P.NV;
+  float* ctab = reinterpret_cast<float*>(smem);
+  float* coef = reinterpret_cast<float*>(smem + P.c_bytes);
+  int* slot_comp = reinterpret_cast<int*>(coef + 256);
+  const int T = d.n_types;
+  const int64_t off_c = T + d.n_lin;
+  for (int k = threadIdx.x; k < P.NC; k += blockDim.x) ctab[k] = d.theta_f[off_c + k];
+  for (int k = threadIdx.x; k < d.n_coef; k += blockDim.x) coef[k] = d.coef_f[k];
+  // slot -> value index of the moment component (monomial-major order of the moment pass)
+  for (int s = threadIdx.x; s < Sh::NCOMP; s += blockDim.x) {
+    // recompute slot s -> comp on the device (same order as make_slots)
+    int ss = 0, comp = 0;
+    for (int k = 0; k < Sh::NMONO && ss <= s; ++k) {
+      int dk = 0;
+      while (nmono_upto(dk) <= k) ++dk;
+      for (int mu = 0; mu < NR; ++mu)
+        if (dk <= Sh::numax(mu)) {
+          if (ss == s) comp = Sh::comp_base(mu) + k;
+          ++ss;
+        }
+    }
+    slot_comp[s] = comp;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* wbase = smem + P.c_bytes + P.tab_bytes + warp * P.warp_bytes;
+  float* vals = reinterpret_cast<float*>(wbase);
+  float* grads = vals + NV;
+  float* GMb = grads + NV;          // 32 x NR
+  float* PQb = GMb + 32 * NR;       // 32 x NQ
+  float* CB = PQb + 32 * NQ;        // CBN
+  int* ZJ = reinterpret_cast<int*>(CB + CBN);
+  __syncthreads();
+  const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
+
+  for (int64_t wk = static_cast<int64_t>(blockIdx.x) * kWarpsF + warp; wk < P.n_work;
+       wk += static_cast<int64_t>(gridDim.x) * kWarpsF) {
+    const int64_t i = P.o.atom_list ? P.o.atom_list[wk] : wk;
+    const int zi = P.type[i];
+    const int64_t p0 = P.nb.off[i];
+    const int np = static_cast<int>(P.nb.off[i + 1] - p0);
+    const float* czi = ctab + static_cast<size_t>(zi) * T * NR * NQ;
+    for (int c = lane; c < Sh::NCOMP; c += 32) vals[c] = 0.f;
+    if (MODE & F_ROWS)
+      for (int e = lane; e < CBN; e += 32) CB[e] = 0.f;
+    __syncwarp();
+    // ---------------- moments (eq. 3) ----------------
+    for (int base = 0; base < np; base += 32) {
+      const bool act = base + lane < np;
+      float rx = 1.f, ry = 0.f, rz = 0.f, rr = 1.f;
+      int zj = 0;
+      if (act) {
+        const int64_t p = p0 + base + lane;
+        const float4 v = P.nb.pr32[p];
+        rx = v.x; ry = v.y; rz = v.z; rr = v.w;
+        zj = P.type[P.nb.pj[p]];
+      }
+      float f[NR], df[NR];
+      radial<NR>(rr, czi + zj * NR * NQ, NQ, rmin, rcut, f, df, nullptr);
+      if (!act)
+#pragma unroll
+        for (int mu = 0; mu < NR; ++mu) f[mu] = 0.f;
+      moments_pass<NR, NU0>(rx, ry, rz, f, vals, slot_comp, lane);
+    }
+    __syncwarp();
+    // ---------------- forward contraction (eqs. 5-6) ----------------
+    for (int wv = 0; wv < d.n_fwaves; ++wv) {
+      const int e1 = d.fwave_ptr[wv + 1];
+      for (int e = d.fwave_ptr[wv] + lane; e < e1; e += 32) {
+        const int dst = d.fdst[e];
+        const int t0 = d.tri_ptr[dst - d.first_dst], t1 = d.tri_ptr[dst - d.first_dst + 1];
+        float acc = 0.f;
+        for (int t = t0; t < t1; ++t) {
+          const uint32_t w = d.tri_pk[t];
+          acc = fmaf(coef[w >> 24], vals[w & 4095u] * vals[(w >> 12) & 4095u], acc);
+        }
+        vals[dst] = acc;
+      }
+      __syncwarp();
+    }
+    // ---------------- site energy (eq. 2) ----------------
+    if (MODE & F_EFS) {
+      float acc = 0.f;
+      for (int a = lane; a < d.n_lin; a += 32) acc = fmaf(d.theta_f[T + a], vals[d.basis_idx[a]], acc);
+      for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+      if (lane == 0) P.o.V[i] = static_cast<double>(acc) + d.theta_d[zi];
+    }
+    // ---------------- adjoint of the contraction (gather form) ----------------
+    for (int wv = 0; wv < d.n_rwaves; ++wv) {
+      const int e1 = d.rwave_ptr[wv + 1];
+      for (int e = d.rwave_ptr[wv] + lane; e < e1; e += 32) {
+        const int x = d.rval[e];
+        float g = d.seed_f[x];
+        const int u1 = d.use_ptr[x + 1];
+        for (int u = d.use_ptr[x]; u < u1; ++u) {
+          const uint32_t w = d.use_pk[u];
+          g = fmaf(coef[w >> 24], vals[w & 4095u] * grads[(w >> 12) & 4095u], g);
+        }
+        grads[x] = g;
+      }
+      __syncwarp();
+    }
+    // ---------------- per-pair adjoint: dV/dr_ij, virial, radial block of b_i ----------------
+    double Wacc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Wacc[k] = 0.0;
+    for (int base = 0; base < np; base += 32) {
+      const bool act = base + lane < np;
+      float rx = 1.f, ry = 0.f, rz = 0.f, rr = 1.f;
+      int zj = 0;
+      const int64_t p = p0 + base + lane;
+      if (act) {
+        const float4 v = P.nb.pr32[p];
+        rx = v.x; ry = v.y; rz = v.z; rr = v.w;
+        zj = P.type[P.nb.pj[p]];
+      }
+      float f[NR], df[NR], g[NR];
+      radial<NR>(rr, czi + zj * NR * NQ, NQ, rmin, rcut, f, df, (MODE & F_ROWS) ? PQb + NQ * lane : nullptr);
+#pragma unroll
+      for (int mu = 0; mu < NR; ++mu) g[mu] = 0.f;
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+      adjoint_pass<NR, NU0>(rx, ry, rz, f, grads, g, gx, gy, gz);
+      if (!act)
+#pragma unroll
+        for (int mu = 0; mu < NR; ++mu) g[mu] = 0.f;
+      if (MODE & F_ROWS) {
+#pragma unroll
+        for (int mu = 0; mu < NR; ++mu) GMb[NR * lane + mu] = g[mu];
+        ZJ[lane] = zj;
+      }
+      if ((MODE & F_EFS) && act) {
+        float rad = 0.f;
+#pragma unroll
+        for (int mu = 0; mu < NR; ++mu) rad = fmaf(g[mu], df[mu], rad);
+        const float s = rad / rr;
+        gx = fmaf(s, rx, gx); gy = fmaf(s, ry, gy); gz = fmaf(s, rz, gz);
+        float* Gout = static_cast<float*>(P.o.G);
+        Gout[3 * p + 0] = gx;
+        Gout[3 * p + 1] = gy;
+        Gout[3 * p + 2] = gz;
+        const double g3[3] = {gx, gy, gz}, r3[3] = {rx, ry, rz};
+#pragma unroll
+        for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+          for (int b2 = 0; b2 < 3; ++b2) Wacc[3 * a2 + b2] -= g3[a2] * r3[b2];
+      }
+      __syncwarp();
+      if (MODE & F_ROWS) {
+        const int nq = min(32, np - base);
+        for (int e = lane; e < CBN; e += 32) {
+          const int zj2 = e / (NR * NQ);
+          const int mu = (e / NQ) % NR;
+          const int b = e % NQ;
+          float acc = 0.f;
+          for (int qq = 0; qq < nq; ++qq)
+            if (ZJ[qq] == zj2) acc = fmaf(GMb[NR * qq + mu], PQb[NQ * qq + b], acc);
+          CB[e] += acc;
+        }
+      }
+      __syncwarp();
+    }
+    if (MODE & F_EFS) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        double v = Wacc[k];
+        for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+        Wacc[k] = v;
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) P.o.Wat[9 * i + k] = Wacc[k];
+    }
+    if (MODE & F_ROWS) {
+      const int64_t ld = P.o.rows_ld;
+      const int cb_total = T * CBN;
+      float* hi = P.o.rows_hi + wk * ld;
+      float* lo = P.o.rows_lo ? P.o.rows_lo + wk * ld : nullptr;
+      double* out64 = P.o.rows ? P.o.rows + wk * ld : nullptr;
+      auto put = [&](int64_t k, float v) {
+        if (out64) out64[k] = v;
+        if (hi) {
+          float h = v;
+          if (lo) {
+            h = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+            lo[k] = v - h;
+          }
+          hi[k] = h;
+        }
+      };
+      for (int k = lane; k < T; k += 32) put(k, (k == zi) ? 1.f : 0.f);
+      for (int a = lane; a < d.n_lin; a += 32) put(T + a, vals[d.basis_idx[a]]);
+      for (int e = lane; e < cb_total; e += 32) {
+        const int zblk = e / CBN;
+        put(off_c + e, (zblk == zi) ? CB[e - zblk * CBN] : 0.f);
+      }
+      for (int64_t k = d.n_params + lane; k < ld; k += 32) put(k, 0.f);
+    }
+    __syncwarp();
+  }
+}
+
+template <int NR, int NU0, int MODE>
+void launch_fast(FastParams P, cudaStream_t s) {
+  auto kern = site_fast_kernel<NR, NU0, MODE>;
+  MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(P.total)));
+  int dev = 0, nsm = 0, per_sm = 0;
+  MTP_CUDA(cudaGetDevice(&dev));
+  MTP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  MTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsF * 32, P.total));
+  per_sm = std::max(per_sm, 1);
+  const int64_t need = (P.n_work + kWarpsF - 1) / kWarpsF;
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(nsm) * per_sm)));
+  if (P.n_work == 0) return;
+  ProfRegion pr((MODE & F_EFS) ? ((MODE & F_ROWS) ? "site_efs_rows" : "site_efs") : "site_rows", s);
+  kern<<<grid, kWarpsF * 32, P.total, s>>>(P);
+  MTP_CUDA(cudaGetLastError());
+}
+
+template <int NR, int NU0>
+void dispatch_mode(FastParams P, bool efs, bool rows, cudaStream_t s) {
+  if (efs && rows) launch_fast<NR, NU0, F_EFS | F_ROWS>(P, s);
+  else if (efs) launch_fast<NR, NU0, F_EFS>(P, s);
+  else launch_fast<NR, NU0, F_ROWS>(P, s);
+}
+
+}  // namespace
+
+// Returns false when the model's shape has no specialised instantiation (the caller then uses
+// the generic kernel).
+bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const SiteOutputs& o, cudaStream_t s) {
+  const DevSchedule& d = m->ds;
+  if (!d.tri_pk || d.n_q > 32) return false;
+  const bool efs = o.V != nullptr;
+  const bool rows = o.rows != nullptr || o.rows_hi != nullptr;
+  if (!efs && !rows) return false;
+  FastParams P{};
+  P.d = d;
+  P.nb = nb->dn;
+  P.type = b->type;
+  P.n_work = o.atom_list ? o.n_list : nb->n_atoms;
+  P.o = o;
+  P.NQ = d.n_q;
+  P.CBN = d.n_types * d.n_rad * d.n_q;
+  P.NC = d.n_types * P.CBN;
+  P.NV = d.n_vals;
+  P.c_bytes = (static_cast<size_t>(P.NC) * sizeof(float) + 15) & ~size_t(15);
+  P.tab_bytes = ((256 + d.n_mom) * sizeof(float) + 15) & ~size_t(15);
+  P.warp_bytes = ((2 * static_cast<size_t>(P.NV) + 32 * (d.n_rad + d.n_q) + P.CBN) * sizeof(float) + 32 * sizeof(int) + 15) &
+                 ~size_t(15);
+  P.total = P.c_bytes + P.tab_bytes + kWarpsF * P.warp_bytes;
+  if (P.total > 227 * 1024) return false;
+  const int nu0 = d.nu_max, nr = d.n_rad;
+  if (nr == 2 && nu0 == 2) { dispatch_mode<2, 2>(P, efs, rows, s); return true; }
+  if (nr == 3 && nu0 == 4) { dispatch_mode<3, 4>(P, efs, rows, s); return true; }
+  if (nr == 4 && nu0 == 6) { dispatch_mode<4, 6>(P, efs, rows, s); return true; }
+  if (nr == 5 && nu0 == 8) { dispatch_mode<5, 8>(P, efs, rows, s); return true; }
+  return false;
+}
+
+}  // namespace mtp

@@ -285,3 +285,26 @@ def test_train_step_loss_and_gradient(api, prec):
     tol = FP64_TOL if prec == "fp64" else 1e-5
     assert loss == pytest.approx(L_ref, rel=tol)
     assert np.abs(grad - grad_ref).max() <= tol * 10 * np.abs(grad_ref).max()
+
+
+# ---------------------------------------------------------------------------------
+# the level-20 ternary model of the MD-scale workload, on a small cell
+# ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_efs_and_rows_level20_ternary(api, prec):
+    bnp = synth.fcc_ternary(seed=12, n=3)
+    md = O.OracleModel(3, 20, 2.0, 5.0)
+    theta = theta_for(md, 44, nbar=42.0)
+    ref = O.efs(md, theta, bnp)
+    model, b, nb, out = run_efs(api, api.make_desc(3, 20), theta, bnp, prec)
+    check_efs(out, ref, len(bnp["type"]), prec)
+    atoms = torch.tensor([0, 7, 50, 107], dtype=torch.int64)
+    rows = api.mtp_param_rows(model, b, nb, prec, atoms).cpu().numpy()
+    rref = O.site_rows(md, theta, bnp["type"], ref["nbr"], req=atoms.numpy())
+    if prec == "fp64":
+        np.testing.assert_allclose(rows, rref, rtol=FP64_TOL, atol=FP64_TOL * np.abs(rref).max())
+    else:
+        # FP32 rows: each entry within a few FP32 rounding units of the row's scale
+        err = np.abs(rows - rref) / np.abs(rref).max(axis=1, keepdims=True)
+        assert err.max() < 2e-5, err.max()
