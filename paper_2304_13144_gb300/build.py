@@ -64,7 +64,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         list(ex.map(run, cmds))
     if cmds or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 

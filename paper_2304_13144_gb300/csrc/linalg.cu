@@ -102,15 +102,16 @@ __global__ void k_inverse_cols(const double* LU, const int* piv, int64_t m, doub
   }
 }
 
-// Split A^-1 into TF32-exact hi and FP32 lo parts, transposed to K-major [n][k] with padding.
+// Split A^-1 into TF32 pieces hi + lo (each rounded to nearest TF32), transposed to K-major
+// [n][k] and zero-padded to ld x ld: the B operand of the tensor-core grade.
 __global__ void k_split_ainv(const double* X, int64_t m, int64_t ld, float* hi, float* lo) {
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (idx >= ld * ld) return;
   const int64_t n = idx / ld, k = idx % ld;   // output row n (= column of A^-1), col k
   const double v = (n < m && k < m) ? X[k * m + n] : 0.0;
-  float h = __uint_as_float(__float_as_uint(static_cast<float>(v)) & 0xffffe000u);
+  const float h = tf32_rn(static_cast<float>(v));
   hi[idx] = h;
-  lo[idx] = static_cast<float>(v - static_cast<double>(h));
+  lo[idx] = tf32_rn(static_cast<float>(v - static_cast<double>(h)));
 }
 
 // Grade product with fused row epilogue.  Block: 256 threads, 64 rows; column tiles of 64;
@@ -215,7 +216,7 @@ void run_lu_inverse(mtp_model* md, const double* A, int64_t m, cudaStream_t s) {
   k_inverse_cols<<<static_cast<unsigned>((m + 63) / 64), 64, 0, s>>>(LU, piv, m, md->ainv_d.as<double>());
   MTP_CUDA(cudaGetLastError());
   // mixed-path copies: K-major padded split (tensor cores) and plain FP32 (SIMT)
-  const int64_t ld = ((m + 127) / 128) * 128;
+  const int64_t ld = grade_tc_ld(m);
   md->ainv_ld = ld;
   md->ainv_f.ensure((2 * ld * ld + m * m) * sizeof(float), s);
   float* hi = md->ainv_f.as<float>();

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -100,6 +101,21 @@ struct DevNbr {
   const int* atom_cfg;  // configuration of each atom
 };
 
+// Round an FP32 value to the nearest TF32 (10 explicit mantissa bits, ties away from zero);
+// the result is exactly representable, so tensor cores consume it without further rounding.
+inline __host__ __device__ float tf32_rn(float x) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+#else
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u = (u + 0x1000u) & 0xffffe000u;
+  float y;
+  std::memcpy(&y, &u, 4);
+  return y;
+#endif
+}
+
 inline __host__ __device__ int pack_img(int a, int b, int c) {
   return (a & 1023) | ((b & 1023) << 10) | ((c & 1023) << 20);
 }
@@ -195,5 +211,6 @@ void run_train_prep(const mtp_nbr* nb, int n_cfg, const double* E, const double*
                     double w_f, double w_s, double* coef, double* U, double* Scfg, double* loss,
                     DevBuf& tmp, cudaStream_t s);
 void run_sum_rows(const double* part, int nrows, int64_t m, double* out, cudaStream_t s);
+int64_t grade_tc_ld(int64_t m);   // row stride of the split parameter rows and of A^-1
 
 }  // namespace mtp

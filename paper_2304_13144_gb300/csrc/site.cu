@@ -414,8 +414,8 @@ __global__ void __launch_bounds__(kWarps * 32) site_kernel(SiteParams P) {
         auto put = [&](int64_t k, double v) {
           float h = static_cast<float>(v);
           if (lo) {
-            h = __uint_as_float(__float_as_uint(h) & 0xffffe000u);
-            lo[k] = static_cast<float>(v - static_cast<double>(h));
+            h = tf32_rn(h);
+            lo[k] = tf32_rn(static_cast<float>(v - static_cast<double>(h)));
           }
           hi[k] = h;
         };

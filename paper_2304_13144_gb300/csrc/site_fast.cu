@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(kWarpsF * 32, 3) site_fast_kernel(FastParams P
         if (hi) {
           float h = v;
           if (lo) {
-            h = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
-            lo[k] = v - h;
+            h = tf32_rn(v);
+            lo[k] = tf32_rn(v - h);
           }
           hi[k] = h;
         }

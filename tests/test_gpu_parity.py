@@ -23,6 +23,32 @@ def api(native_lib):
     return A
 
 
+def tf32_rn(x):
+    """Round FP32 values to the nearest TF32 (ties away from zero), as the library's split does."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def tf32_split(x):
+    """Return the (hi, lo) TF32 pieces of x as an exact float64 sum hi + lo, with the product
+    structure of the tensor-core grade folded in by the caller (hi.hi + hi.lo + lo.hi)."""
+    hi = tf32_rn(x)
+    lo = tf32_rn((x - hi).astype(np.float32))
+    return SplitPair(hi.astype(np.float64), lo.astype(np.float64))
+
+
+class SplitPair:
+    def __init__(self, hi, lo):
+        self.hi, self.lo = hi, lo
+
+    @property
+    def T(self):
+        return SplitPair(self.hi.T, self.lo.T)
+
+    def __matmul__(self, other):
+        return self.hi @ other.hi + self.hi @ other.lo + self.lo @ other.hi
+
+
 def theta_for(md, seed, nbar=40.0, kappa=10.0):
     nu_sum = [sum(nu for _, nu in labs) for labs, _ in md.basis]
     nf = [len(labs) for labs, _ in md.basis]
@@ -198,9 +224,13 @@ def test_grade_is_one_on_active_set_and_flags(api):
     nb = api.mtp_build_neighbors(model, b)
     api.mtp_set_active_set(model, torch.tensor(A, device="cuda"))
     ref_g, _ = O.grade(A, rows)
-    # The mixed path forms b_i in FP32: rounding the exact rows to FP32 alone moves gamma by
-    # this much for this (ill-conditioned, kappa ~ 1e7) active set; the gate allows 4x that.
-    floor = np.abs(O.grade(A, rows.astype(np.float32).astype(np.float64))[0] - ref_g)
+    # The mixed path forms b_i in FP32 and the product from TF32 pieces: representing the exact
+    # rows and A^-1 that way alone moves gamma by `floor` for this (ill-conditioned, kappa ~ 1e7)
+    # active set; the gate allows 4x that.
+    Ainv = np.linalg.inv(A)
+    C = tf32_split(rows.astype(np.float32)) @ tf32_split(Ainv.astype(np.float32)).T
+    floor = np.abs(np.abs(C).max(axis=1) - ref_g)
+    floor = np.maximum(floor, np.abs(O.grade(A, rows.astype(np.float32).astype(np.float64))[0] - ref_g))
     for prec in ("fp64", "mixed"):
         out = api.mtp_grade(model, b, nb, prec, threshold=2.0)
         g = out["gamma"].cpu().numpy()
@@ -308,3 +338,27 @@ def test_efs_and_rows_level20_ternary(api, prec):
         # FP32 rows: each entry within a few FP32 rounding units of the row's scale
         err = np.abs(rows - rref) / np.abs(rref).max(axis=1, keepdims=True)
         assert err.max() < 2e-5, err.max()
+
+
+@pytest.mark.parametrize("T,lev,n", [(3, 16, 8), (1, 8, 9)])
+def test_tensor_core_grade_matches_fp64_path(api, T, lev, n):
+    """Many 128-row tiles with a ragged last tile; one or two 224-column passes."""
+    bnp = synth.fcc_ternary(seed=21, n=n)
+    bnp["type"] = bnp["type"] % T
+    md = O.OracleModel(T, lev, 2.0, 5.0)
+    theta = theta_for(md, 9)
+    model = api.mtp_load(api.make_desc(T, lev), theta)
+    b = api.Batch(bnp)
+    nb = api.mtp_build_neighbors(model, b)
+    api.mtp_set_active_set(model, torch.tensor(synth.diag_dominant(3, md.m), device="cuda"))
+    g64 = api.mtp_grade(model, b, nb, "fp64", threshold=1.0)
+    gmx = api.mtp_grade(model, b, nb, "mixed", threshold=1.0)
+    a, c = g64["gamma"].cpu().numpy(), gmx["gamma"].cpu().numpy()
+    assert np.all(np.isfinite(c)) and len(c) == len(bnp["type"])
+    assert np.all(np.abs(a - c) <= 1e-4 * np.maximum(1.0, a))
+    # argmax agrees wherever the top two entries are well separated (checked on FP64 rows)
+    rows = api.mtp_param_rows(model, b, nb, "fp64").cpu().numpy()
+    Cf = np.abs(rows @ np.linalg.inv(synth.diag_dominant(3, md.m)))
+    top2 = np.sort(Cf, axis=1)[:, -2:]
+    clear = (top2[:, 1] - top2[:, 0]) > 1e-3 * top2[:, 1]
+    assert (gmx["argmax"].cpu().numpy()[clear] == g64["argmax"].cpu().numpy()[clear]).all()
