@@ -43,6 +43,57 @@ size_t put(std::vector<char>& blob, const std::vector<T>& v) {
 
 }  // namespace
 
+namespace {
+
+// Orders the terms of one round (lists[l] for lanes l) into L iterations so that, at each
+// iteration, the 32 lanes' two shared-memory operands fall into distinct banks as far as a
+// greedy choice allows (same address = broadcast, free).  `bank_a/b` map a word to the
+// word offset it reads; `swap` (optional) may exchange the two operands of a word.
+template <class BankA, class BankB, class Swap>
+std::vector<std::vector<uint32_t>> bank_order(std::vector<std::vector<uint32_t>> lists, int L, BankA bank_a,
+                                              BankB bank_b, Swap swap) {
+  std::vector<std::vector<uint32_t>> out(lists.size());
+  for (int it = 0; it < L; ++it) {
+    std::vector<std::vector<uint32_t>> addr_a(32), addr_b(32);
+    auto cost = [&](uint32_t w) {
+      const uint32_t oa = bank_a(w), ob = bank_b(w);
+      int c = 0;
+      auto& va = addr_a[oa & 31];
+      if (std::find(va.begin(), va.end(), oa) == va.end()) c += static_cast<int>(va.size());
+      auto& vb = addr_b[ob & 31];
+      if (std::find(vb.begin(), vb.end(), ob) == vb.end()) c += static_cast<int>(vb.size());
+      return c;
+    };
+    for (size_t l = 0; l < lists.size(); ++l) {
+      auto& lst = lists[l];
+      if (lst.empty()) continue;
+      size_t best = 0;
+      int bestc = 1 << 30;
+      bool best_sw = false;
+      for (size_t k = 0; k < lst.size(); ++k) {
+        const int c0 = cost(lst[k]);
+        if (c0 < bestc) { bestc = c0; best = k; best_sw = false; }
+        const uint32_t ws = swap(lst[k]);
+        if (ws != lst[k]) {
+          const int c1 = cost(ws);
+          if (c1 < bestc) { bestc = c1; best = k; best_sw = true; }
+        }
+        if (bestc == 0) break;
+      }
+      const uint32_t w = best_sw ? swap(lst[best]) : lst[best];
+      lst.erase(lst.begin() + static_cast<long>(best));
+      auto& va = addr_a[bank_a(w) & 31];
+      if (std::find(va.begin(), va.end(), bank_a(w)) == va.end()) va.push_back(bank_a(w));
+      auto& vb = addr_b[bank_b(w) & 31];
+      if (std::find(vb.begin(), vb.end(), bank_b(w)) == vb.end()) vb.push_back(bank_b(w));
+      out[l].push_back(w);
+    }
+  }
+  return out;
+}
+
+}  // namespace
+
 // Uploads the schedule with its forward waves (destinations grouped by dependency depth) and
 // the transposed triple list for the adjoint (uses of each value, grouped by height).
 void upload_schedule(mtp_model* md) {
@@ -112,18 +163,61 @@ void upload_schedule(mtp_model* md) {
   std::vector<double> coefs(S.tri_c.begin(), S.tri_c.end());
   std::sort(coefs.begin(), coefs.end());
   coefs.erase(std::unique(coefs.begin(), coefs.end()), coefs.end());
-  const bool packable = nv <= 4096 && coefs.size() <= 256;
+  const bool packable = nv <= 4096 && coefs.size() <= 255;
   std::vector<uint32_t> tri_pk, use_pk;
   std::vector<float> coef_f(coefs.begin(), coefs.end());
+  coef_f.push_back(0.0f);   // coefficient of the padding terms
+  const uint32_t zero_ci = static_cast<uint32_t>(coef_f.size() - 1);
+  std::vector<uint32_t> fslab, rslab;
+  std::vector<int> fr_dst, rr_val;
+  std::vector<int> fround, rround;   // 4 ints per round
   if (packable) {
     auto ci = [&](double c) { return static_cast<uint32_t>(std::lower_bound(coefs.begin(), coefs.end(), c) - coefs.begin()); };
     for (size_t t = 0; t < S.tri_a.size(); ++t)
       tri_pk.push_back(static_cast<uint32_t>(S.tri_a[t]) | (static_cast<uint32_t>(S.tri_b[t]) << 12) | (ci(S.tri_c[t]) << 24));
     for (size_t u = 0; u < use_od.size(); ++u)
       use_pk.push_back((use_od[u] & 0xffffu) | ((use_od[u] >> 16) << 12) | (ci(use_cd[u]) << 24));
+    const uint32_t pad = zero_ci << 24;   // 0 * v[0] * v[0]
+    // forward slabs: waves of destinations, rounds of 32 (already sorted by length, descending)
+    for (int wv = 0; wv + 1 < static_cast<int>(fwave_ptr.size()); ++wv)
+      for (int e0 = fwave_ptr[wv]; e0 < fwave_ptr[wv + 1]; e0 += 32) {
+        const int e1 = std::min(e0 + 32, fwave_ptr[wv + 1]);
+        int L = 0;
+        for (int e = e0; e < e1; ++e) L = std::max(L, S.dst_ptr[fdst[e] - nm + 1] - S.dst_ptr[fdst[e] - nm]);
+        fround.insert(fround.end(), {L, static_cast<int>(fslab.size()), e1 == fwave_ptr[wv + 1] ? 1 : 0, 0});
+        for (int l = 0; l < 32; ++l) fr_dst.push_back(e0 + l < e1 ? fdst[e0 + l] : -1);
+        std::vector<std::vector<uint32_t>> lists(32);
+        for (int e = e0; e < e1; ++e)
+          for (int t = S.dst_ptr[fdst[e] - nm]; t < S.dst_ptr[fdst[e] - nm + 1]; ++t) lists[e - e0].push_back(tri_pk[t]);
+        auto ord = bank_order(
+            lists, L, [](uint32_t w) { return w & 4095u; }, [](uint32_t w) { return (w >> 12) & 4095u; },
+            [](uint32_t w) { return (w & 0xff000000u) | ((w & 4095u) << 12) | ((w >> 12) & 4095u); });
+        for (int it = 0; it < L; ++it)
+          for (int l = 0; l < 32; ++l) fslab.push_back(it < static_cast<int>(ord[l].size()) ? ord[l][it] : pad);
+      }
+    // reverse slabs: waves of values by height, rounds of 32 (sorted by number of uses)
+    for (int wv = 0; wv + 1 < static_cast<int>(rwave_ptr.size()); ++wv)
+      for (int e0 = rwave_ptr[wv]; e0 < rwave_ptr[wv + 1]; e0 += 32) {
+        const int e1 = std::min(e0 + 32, rwave_ptr[wv + 1]);
+        int L = 0;
+        for (int e = e0; e < e1; ++e) L = std::max(L, static_cast<int>(uses[rval[e]].size()));
+        rround.insert(rround.end(), {L, static_cast<int>(rslab.size()), e1 == rwave_ptr[wv + 1] ? 1 : 0, 0});
+        for (int l = 0; l < 32; ++l) rr_val.push_back(e0 + l < e1 ? rval[e0 + l] : -1);
+        std::vector<std::vector<uint32_t>> lists(32);
+        for (int e = e0; e < e1; ++e)
+          for (int u = use_ptr[rval[e]]; u < use_ptr[rval[e] + 1]; ++u) lists[e - e0].push_back(use_pk[u]);
+        const uint32_t gofs = static_cast<uint32_t>(nv);   // grads follow vals in shared memory
+        auto ord = bank_order(
+            lists, L, [](uint32_t w) { return w & 4095u; }, [gofs](uint32_t w) { return gofs + ((w >> 12) & 4095u); },
+            [](uint32_t w) { return w; });
+        for (int it = 0; it < L; ++it)
+          for (int l = 0; l < 32; ++l) rslab.push_back(it < static_cast<int>(ord[l].size()) ? ord[l][it] : pad);
+      }
   }
   std::vector<char> blob;
   const size_t o_tpk = put(blob, tri_pk), o_upk = put(blob, use_pk), o_cf = put(blob, coef_f);
+  const size_t o_fs = put(blob, fslab), o_fr = put(blob, fround), o_frd = put(blob, fr_dst), o_rs = put(blob, rslab),
+               o_rr = put(blob, rround), o_rrv = put(blob, rr_val);
   const size_t o_ci = put(blob, comp_info), o_fwp = put(blob, fwave_ptr), o_fd = put(blob, fdst),
                o_tp = put(blob, S.dst_ptr), o_tab = put(blob, tri_ab), o_tcf = put(blob, tri_cf),
                o_tcd = put(blob, S.tri_c), o_rwp = put(blob, rwave_ptr), o_rv = put(blob, rval),
@@ -156,6 +250,18 @@ void upload_schedule(mtp_model* md) {
   D.use_pk = packable ? reinterpret_cast<const uint32_t*>(base + o_upk) : nullptr;
   D.coef_f = reinterpret_cast<const float*>(base + o_cf);
   D.n_coef = static_cast<int>(coef_f.size());
+  D.n_tri = static_cast<int>(S.tri_a.size());
+  D.fslab = reinterpret_cast<const uint32_t*>(base + o_fs);
+  D.fround = reinterpret_cast<const int4*>(base + o_fr);
+  D.fr_dst = reinterpret_cast<const int*>(base + o_frd);
+  D.n_fround = static_cast<int>(fround.size() / 4);
+  D.fslab_words = static_cast<int>(fslab.size());
+  D.rslab = reinterpret_cast<const uint32_t*>(base + o_rs);
+  D.rround = reinterpret_cast<const int4*>(base + o_rr);
+  D.rr_val = reinterpret_cast<const int*>(base + o_rrv);
+  D.n_rround = static_cast<int>(rround.size() / 4);
+  D.rslab_words = static_cast<int>(rslab.size());
+  D.n_use = static_cast<int>(use_od.size());
 }
 
 void upload_theta(mtp_model* md) {

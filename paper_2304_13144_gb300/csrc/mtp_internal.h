@@ -72,6 +72,18 @@ struct DevSchedule {
   const uint32_t* use_pk;
   const float* coef_f;
   int n_coef;
+  int n_tri, n_use;         // lengths of the triple and use lists
+  // "slab" form of the packed lists for warp-per-neighborhood execution: rounds of 32
+  // destinations; word (round r, iteration it, lane l) at off_r + 32 it + l, lists padded to the
+  // round's longest with zero-coefficient terms.  round = {L, off, end_of_wave, 0}
+  const uint32_t* fslab;
+  const int4* fround;
+  const int* fr_dst;        // [n_fround * 32], -1 = idle lane
+  int n_fround, fslab_words;
+  const uint32_t* rslab;
+  const int4* rround;
+  const int* rr_val;        // [n_rround * 32], -1 = idle lane
+  int n_rround, rslab_words;
   const double* theta_d;    // [n_params]
   const float* theta_f;
   const double* seed_d;     // [n_vals] sum of xi over basis functions stored at that value

@@ -129,8 +129,14 @@ struct FastParams {
   int64_t n_work;
   SiteOutputs o;
   int NQ, CBN, NC, NV;
-  size_t c_bytes, tab_bytes, warp_bytes, total;
+  size_t c_bytes, tab_bytes, sched_bytes, warp_bytes, total;
+  // word offsets of the schedule arrays inside the shared-memory copy
+  int o_fslab, o_fround, o_frdst, o_rslab, o_rround, o_rrval, o_seed;
 };
+
+__device__ __forceinline__ void copy_words(uint32_t* dst, const uint32_t* src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
 
 // radial functions f_mu, f'_mu (eq. 4) for one pair; Q_b written to Qrow if given
 template <int NR>
@@ -236,11 +242,11 @@ __device__ __forceinline__ void adjoint_pass(float rx, float ry, float rz, const
   });
 }
 
-constexpr int kWarpsF = 4;
+constexpr int kMaxWarpsF = 8;
 enum : int { F_EFS = 1, F_ROWS = 2 };
 
 template <int NR, int NU0, int MODE>
-__global__ void __launch_bounds__(kWarpsF * 32, 3) site_fast_kernel(FastParams P) {
+__global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParams P) {
   using Sh = Shape<NR, NU0>;
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
@@ -267,10 +273,29 @@ __global__ void __launch_bounds__(kWarpsF * 32, 3) site_fast_kernel(FastParams P
     }
     slot_comp[s] = comp;
   }
+  // the contraction schedule, staged once per (persistent) block: every warp reads it per atom
+  uint32_t* sched = reinterpret_cast<uint32_t*>(smem + P.c_bytes + P.tab_bytes);
+  copy_words(sched + P.o_fslab, d.fslab, d.fslab_words);
+  copy_words(sched + P.o_fround, reinterpret_cast<const uint32_t*>(d.fround), 4 * d.n_fround);
+  copy_words(sched + P.o_frdst, reinterpret_cast<const uint32_t*>(d.fr_dst), 32 * d.n_fround);
+  copy_words(sched + P.o_rslab, d.rslab, d.rslab_words);
+  copy_words(sched + P.o_rround, reinterpret_cast<const uint32_t*>(d.rround), 4 * d.n_rround);
+  copy_words(sched + P.o_rrval, reinterpret_cast<const uint32_t*>(d.rr_val), 32 * d.n_rround);
+  copy_words(sched + P.o_seed, reinterpret_cast<const uint32_t*>(d.seed_f), d.n_vals);
+  const uint32_t* s_fslab = sched + P.o_fslab;
+  const int4* s_fround = reinterpret_cast<const int4*>(sched + P.o_fround);
+  const int* s_frdst = reinterpret_cast<const int*>(sched + P.o_frdst);
+  const uint32_t* s_rslab = sched + P.o_rslab;
+  const int4* s_rround = reinterpret_cast<const int4*>(sched + P.o_rround);
+  const int* s_rrval = reinterpret_cast<const int*>(sched + P.o_rrval);
+  const float* s_seed = reinterpret_cast<const float*>(sched + P.o_seed);
+  const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wbase = smem + P.c_bytes + P.tab_bytes + warp * P.warp_bytes;
+  unsigned char* wbase = smem + P.c_bytes + P.tab_bytes + P.sched_bytes + warp * P.warp_bytes;
   float* vals = reinterpret_cast<float*>(wbase);
   float* grads = vals + NV;
+  // padding terms read vals[0] and grads[0]: keep every entry finite from the start
+  for (int k = lane; k < 2 * NV; k += 32) vals[k] = 0.f;
   float* GMb = grads + NV;          // 32 x NR
   float* PQb = GMb + 32 * NR;       // 32 x NQ
   float* CB = PQb + 32 * NQ;        // CBN
@@ -278,8 +303,8 @@ __global__ void __launch_bounds__(kWarpsF * 32, 3) site_fast_kernel(FastParams P
   __syncthreads();
   const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
 
-  for (int64_t wk = static_cast<int64_t>(blockIdx.x) * kWarpsF + warp; wk < P.n_work;
-       wk += static_cast<int64_t>(gridDim.x) * kWarpsF) {
+  for (int64_t wk = static_cast<int64_t>(blockIdx.x) * nwarps + warp; wk < P.n_work;
+       wk += static_cast<int64_t>(gridDim.x) * nwarps) {
     const int64_t i = P.o.atom_list ? P.o.atom_list[wk] : wk;
     const int zi = P.type[i];
     const int64_t p0 = P.nb.off[i];
@@ -308,20 +333,26 @@ __global__ void __launch_bounds__(kWarpsF * 32, 3) site_fast_kernel(FastParams P
       moments_pass<NR, NU0>(rx, ry, rz, f, vals, slot_comp, lane);
     }
     __syncwarp();
-    // ---------------- forward contraction (eqs. 5-6) ----------------
-    for (int wv = 0; wv < d.n_fwaves; ++wv) {
-      const int e1 = d.fwave_ptr[wv + 1];
-      for (int e = d.fwave_ptr[wv] + lane; e < e1; e += 32) {
-        const int dst = d.fdst[e];
-        const int t0 = d.tri_ptr[dst - d.first_dst], t1 = d.tri_ptr[dst - d.first_dst + 1];
-        float acc = 0.f;
-        for (int t = t0; t < t1; ++t) {
-          const uint32_t w = d.tri_pk[t];
-          acc = fmaf(coef[w >> 24], vals[w & 4095u] * vals[(w >> 12) & 4095u], acc);
-        }
-        vals[dst] = acc;
+    // ---------------- forward contraction (eqs. 5-6), slab form ----------------
+    for (int r = 0; r < d.n_fround; ++r) {
+      const int4 rd = s_fround[r];
+      const uint32_t* slab = s_fslab + rd.y + lane;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      int it = 0;
+      for (; it + 4 <= rd.x; it += 4) {
+        const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32], w2 = slab[32 * it + 64], w3 = slab[32 * it + 96];
+        a0 = fmaf(coef[w0 >> 24], vals[w0 & 4095u] * vals[(w0 >> 12) & 4095u], a0);
+        a1 = fmaf(coef[w1 >> 24], vals[w1 & 4095u] * vals[(w1 >> 12) & 4095u], a1);
+        a2 = fmaf(coef[w2 >> 24], vals[w2 & 4095u] * vals[(w2 >> 12) & 4095u], a2);
+        a3 = fmaf(coef[w3 >> 24], vals[w3 & 4095u] * vals[(w3 >> 12) & 4095u], a3);
       }
-      __syncwarp();
+      for (; it < rd.x; ++it) {
+        const uint32_t w0 = slab[32 * it];
+        a0 = fmaf(coef[w0 >> 24], vals[w0 & 4095u] * vals[(w0 >> 12) & 4095u], a0);
+      }
+      const int dst = s_frdst[32 * r + lane];
+      if (dst >= 0) vals[dst] = (a0 + a1) + (a2 + a3);
+      if (rd.z) __syncwarp();
     }
     // ---------------- site energy (eq. 2) ----------------
     if (MODE & F_EFS) {
@@ -330,20 +361,26 @@ __global__ void __launch_bounds__(kWarpsF * 32, 3) site_fast_kernel(FastParams P
       for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
       if (lane == 0) P.o.V[i] = static_cast<double>(acc) + d.theta_d[zi];
     }
-    // ---------------- adjoint of the contraction (gather form) ----------------
-    for (int wv = 0; wv < d.n_rwaves; ++wv) {
-      const int e1 = d.rwave_ptr[wv + 1];
-      for (int e = d.rwave_ptr[wv] + lane; e < e1; e += 32) {
-        const int x = d.rval[e];
-        float g = d.seed_f[x];
-        const int u1 = d.use_ptr[x + 1];
-        for (int u = d.use_ptr[x]; u < u1; ++u) {
-          const uint32_t w = d.use_pk[u];
-          g = fmaf(coef[w >> 24], vals[w & 4095u] * grads[(w >> 12) & 4095u], g);
-        }
-        grads[x] = g;
+    // ---------------- adjoint of the contraction (gather form), slab form ----------------
+    for (int r = 0; r < d.n_rround; ++r) {
+      const int4 rd = s_rround[r];
+      const uint32_t* slab = s_rslab + rd.y + lane;
+      const int x = s_rrval[32 * r + lane];
+      float a0 = x >= 0 ? s_seed[x] : 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      int it = 0;
+      for (; it + 4 <= rd.x; it += 4) {
+        const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32], w2 = slab[32 * it + 64], w3 = slab[32 * it + 96];
+        a0 = fmaf(coef[w0 >> 24], vals[w0 & 4095u] * grads[(w0 >> 12) & 4095u], a0);
+        a1 = fmaf(coef[w1 >> 24], vals[w1 & 4095u] * grads[(w1 >> 12) & 4095u], a1);
+        a2 = fmaf(coef[w2 >> 24], vals[w2 & 4095u] * grads[(w2 >> 12) & 4095u], a2);
+        a3 = fmaf(coef[w3 >> 24], vals[w3 & 4095u] * grads[(w3 >> 12) & 4095u], a3);
       }
-      __syncwarp();
+      for (; it < rd.x; ++it) {
+        const uint32_t w0 = slab[32 * it];
+        a0 = fmaf(coef[w0 >> 24], vals[w0 & 4095u] * grads[(w0 >> 12) & 4095u], a0);
+      }
+      if (x >= 0) grads[x] = (a0 + a1) + (a2 + a3);
+      if (rd.z) __syncwarp();
     }
     // ---------------- per-pair adjoint: dV/dr_ij, virial, radial block of b_i ----------------
     double Wacc[9];
@@ -445,27 +482,27 @@ __global__ void __launch_bounds__(kWarpsF * 32, 3) site_fast_kernel(FastParams P
 }
 
 template <int NR, int NU0, int MODE>
-void launch_fast(FastParams P, cudaStream_t s) {
+void launch_fast(FastParams P, int nwarps, cudaStream_t s) {
   auto kern = site_fast_kernel<NR, NU0, MODE>;
   MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(P.total)));
   int dev = 0, nsm = 0, per_sm = 0;
   MTP_CUDA(cudaGetDevice(&dev));
   MTP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  MTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsF * 32, P.total));
+  MTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nwarps * 32, P.total));
   per_sm = std::max(per_sm, 1);
-  const int64_t need = (P.n_work + kWarpsF - 1) / kWarpsF;
+  const int64_t need = (P.n_work + nwarps - 1) / nwarps;
   const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(nsm) * per_sm)));
   if (P.n_work == 0) return;
   ProfRegion pr((MODE & F_EFS) ? ((MODE & F_ROWS) ? "site_efs_rows" : "site_efs") : "site_rows", s);
-  kern<<<grid, kWarpsF * 32, P.total, s>>>(P);
+  kern<<<grid, nwarps * 32, P.total, s>>>(P);
   MTP_CUDA(cudaGetLastError());
 }
 
 template <int NR, int NU0>
-void dispatch_mode(FastParams P, bool efs, bool rows, cudaStream_t s) {
-  if (efs && rows) launch_fast<NR, NU0, F_EFS | F_ROWS>(P, s);
-  else if (efs) launch_fast<NR, NU0, F_EFS>(P, s);
-  else launch_fast<NR, NU0, F_ROWS>(P, s);
+void dispatch_mode(FastParams P, int nwarps, bool efs, bool rows, cudaStream_t s) {
+  if (efs && rows) launch_fast<NR, NU0, F_EFS | F_ROWS>(P, nwarps, s);
+  else if (efs) launch_fast<NR, NU0, F_EFS>(P, nwarps, s);
+  else launch_fast<NR, NU0, F_ROWS>(P, nwarps, s);
 }
 
 }  // namespace
@@ -492,13 +529,27 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   P.tab_bytes = ((256 + d.n_mom) * sizeof(float) + 15) & ~size_t(15);
   P.warp_bytes = ((2 * static_cast<size_t>(P.NV) + 32 * (d.n_rad + d.n_q) + P.CBN) * sizeof(float) + 32 * sizeof(int) + 15) &
                  ~size_t(15);
-  P.total = P.c_bytes + P.tab_bytes + kWarpsF * P.warp_bytes;
-  if (P.total > 227 * 1024) return false;
+  // shared-memory copy of the schedule (32-bit words)
+  int w = 0;
+  auto take = [&](int n) { const int o = w; w += (n + 3) & ~3; return o; };
+  P.o_fslab = take(d.fslab_words);
+  P.o_fround = take(4 * d.n_fround);
+  P.o_frdst = take(32 * d.n_fround);
+  P.o_rslab = take(d.rslab_words);
+  P.o_rround = take(4 * d.n_rround);
+  P.o_rrval = take(32 * d.n_rround);
+  P.o_seed = take(d.n_vals);
+  P.sched_bytes = static_cast<size_t>(w) * 4;
+  const size_t fixed = P.c_bytes + P.tab_bytes + P.sched_bytes;
+  const size_t limit = 227 * 1024;
+  if (fixed + 2 * P.warp_bytes > limit) return false;
+  const int nwarps = static_cast<int>(std::min<size_t>(kMaxWarpsF, (limit - fixed) / P.warp_bytes));
+  P.total = fixed + nwarps * P.warp_bytes;
   const int nu0 = d.nu_max, nr = d.n_rad;
-  if (nr == 2 && nu0 == 2) { dispatch_mode<2, 2>(P, efs, rows, s); return true; }
-  if (nr == 3 && nu0 == 4) { dispatch_mode<3, 4>(P, efs, rows, s); return true; }
-  if (nr == 4 && nu0 == 6) { dispatch_mode<4, 6>(P, efs, rows, s); return true; }
-  if (nr == 5 && nu0 == 8) { dispatch_mode<5, 8>(P, efs, rows, s); return true; }
+  if (nr == 2 && nu0 == 2) { dispatch_mode<2, 2>(P, nwarps, efs, rows, s); return true; }
+  if (nr == 3 && nu0 == 4) { dispatch_mode<3, 4>(P, nwarps, efs, rows, s); return true; }
+  if (nr == 4 && nu0 == 6) { dispatch_mode<4, 6>(P, nwarps, efs, rows, s); return true; }
+  if (nr == 5 && nu0 == 8) { dispatch_mode<5, 8>(P, nwarps, efs, rows, s); return true; }
   return false;
 }
 
