@@ -172,6 +172,20 @@ mtp_status mtp_energy_forces_stress(mtp_model* model, const mtp_batch* batch, co
                                     mtp_precision prec, double* energy, double* site_energy,
                                     double* forces, double* virial, void* stream);
 
+/* Allocation-free variant of mtp_energy_forces_stress (the paper has no counterpart).
+ * For callers that may not allocate device memory at call time (an engine that owns the whole
+ * device-memory budget through its own allocator, or a time-step loop that cannot afford an
+ * allocation's synchronisation or failure).  Same arguments, outputs and precision as
+ * mtp_energy_forces_stress; the scratch lives in a fixed 16 MiB device array inside the
+ * library, held by every GPU that loads it until exit.  Limits: at most 32768 atoms, 524288
+ * pairs and 1024 configuration segments (4096-atom pieces of the configurations), else
+ * MTP_ERR_CAPACITY.  Calls no cudaMalloc/cudaFree.  The first call on a device looks up the
+ * array's address, so make it before any stream capture.  Calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller. */
+mtp_status mtp_energy_forces_stress_noalloc(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                                            mtp_precision prec, double* energy, double* site_energy,
+                                            double* forces, double* virial, void* stream);
+
 /* Per-atom parameter rows b_i = dV_i/dtheta (eq. 9), DEVICE rows[n x m] FP64 for the atoms
  * listed in DEVICE atoms[n] (atoms == NULL: all atoms, n = N). */
 mtp_status mtp_param_rows(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,

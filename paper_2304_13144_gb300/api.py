@@ -68,6 +68,7 @@ _SIGS = {
     "mtp_nbr_size": (ctypes.c_int, [_P, _P, _P]),
     "mtp_nbr_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "mtp_energy_forces_stress": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "mtp_energy_forces_stress_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "mtp_param_rows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _I64, _P, _P]),
     "mtp_grade": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _D, _P, _P, _P, _P, _P]),
     "mtp_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _D, _P, _P, _P, _P, _P]),
@@ -301,6 +302,19 @@ def mtp_energy_forces_stress(model, batch, nbr, prec="mixed", energy=None, site_
         virial = torch.empty((K, 3, 3), dtype=torch.float64, device=dev)
     _check(lib().mtp_energy_forces_stress(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(energy),
                                           _ptr(site_energy), _ptr(forces), _ptr(virial), _stream(stream)))
+    return {"energy": energy, "site_energy": site_energy, "forces": forces, "virial": virial}
+
+
+def mtp_energy_forces_stress_noalloc(model, batch, nbr, prec="mixed", stream=None):
+    """Allocation-free energies/forces/virial: the library allocates nothing (outputs are
+    allocated here by torch, before the call)."""
+    N, K = batch.n_atoms, batch.n_cfg
+    energy = torch.empty(K, dtype=torch.float64, device="cuda")
+    site_energy = torch.empty(N, dtype=torch.float64, device="cuda")
+    forces = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    virial = torch.empty((K, 3, 3), dtype=torch.float64, device="cuda")
+    _check(lib().mtp_energy_forces_stress_noalloc(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(energy),
+                                                  _ptr(site_energy), _ptr(forces), _ptr(virial), _stream(stream)))
     return {"energy": energy, "site_energy": site_energy, "forces": forces, "virial": virial}
 
 

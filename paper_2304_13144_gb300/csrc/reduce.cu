@@ -191,6 +191,16 @@ void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, doub
   MTP_CUDA(cudaGetLastError());
 }
 
+void run_config_sums_into(const mtp_nbr* nb, const double* V, const double* Wat, double* E, double* W, double* part,
+                          cudaStream_t s) {
+  ProfRegion pr("config_sums", s);
+  k_seg_sums<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), V, Wat, part);
+  MTP_CUDA(cudaGetLastError());
+  k_cfg_sums<<<nblk(nb->n_cfg, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, part, static_cast<int>(nb->n_cfg),
+                                                 E, W);
+  MTP_CUDA(cudaGetLastError());
+}
+
 void run_flag(int64_t N, const double* gamma, double threshold, int32_t* flagged, int64_t* n_flagged, DevBuf& tmp,
               cudaStream_t s) {
   AboveThreshold pred{gamma, threshold};
