@@ -191,8 +191,11 @@ struct Builder {
     const auto& ea = exponents(A.second - k);
     const auto& eb = exponents(B.second - k);
     std::vector<std::vector<int>> table(ea.size(), std::vector<int>(eb.size()));
+    // A x_k A is symmetric under exchange of its two index groups: T[alpha|beta] = T[beta|alpha]
+    const bool sym = (A == B);
     for (size_t i = 0; i < ea.size(); ++i)
       for (size_t j = 0; j < eb.size(); ++j) {
+        if (sym && j < i) { table[i][j] = table[j][i]; continue; }
         std::vector<int> key = {1};
         push_label(key, A); push_label(key, B); key.push_back(k);
         push_exp(key, ea[i]); push_exp(key, eb[j]);

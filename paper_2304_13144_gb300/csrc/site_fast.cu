@@ -139,8 +139,8 @@ __device__ __forceinline__ void copy_words(uint32_t* dst, const uint32_t* src, i
 }
 
 // radial functions f_mu, f'_mu (eq. 4) for one pair; Q_b written to Qrow if given
-template <int NR>
-__device__ __forceinline__ void radial(float rr, const float* cz, int NQ, float rmin, float rcut, float (&f)[NR],
+template <int NR, int NQ>
+__device__ __forceinline__ void radial(float rr, const float* cz, float rmin, float rcut, float (&f)[NR],
                                        float (&df)[NR], float* Qrow) {
   const float x = (2.f * rr - (rmin + rcut)) * (1.f / (rcut - rmin));
   const float w = rcut - rr;
@@ -149,6 +149,7 @@ __device__ __forceinline__ void radial(float rr, const float* cz, int NQ, float 
   float t0 = 1.f, t1 = x, d0 = 0.f, d1 = 1.f;
 #pragma unroll
   for (int mu = 0; mu < NR; ++mu) { f[mu] = 0.f; df[mu] = 0.f; }
+#pragma unroll
   for (int b = 0; b < NQ; ++b) {
     float tb, db;
     if (b == 0) { tb = t0; db = d0; }
@@ -243,6 +244,7 @@ __device__ __forceinline__ void adjoint_pass(float rx, float ry, float rz, const
 }
 
 constexpr int kMaxWarpsF = 8;
+constexpr int kNQ = 8;   // radial polynomials of the specialised kernel (other N_Q: generic kernel)
 enum : int { F_EFS = 1, F_ROWS = 2 };
 
 template <int NR, int NU0, int MODE>
@@ -250,7 +252,8 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
   using Sh = Shape<NR, NU0>;
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
-  const int NQ = P.NQ, CBN = P.CBN, NV = P.NV;
+  constexpr int NQ = kNQ;
+  const int CBN = P.CBN, NV = P.NV;
   float* ctab = reinterpret_cast<float*>(smem);
   float* coef = reinterpret_cast<float*>(smem + P.c_bytes);
   int* slot_comp = reinterpret_cast<int*>(coef + 256);
@@ -291,21 +294,27 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
   const float* s_seed = reinterpret_cast<const float*>(sched + P.o_seed);
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per warp: two neighborhoods carried through the contraction together
   unsigned char* wbase = smem + P.c_bytes + P.tab_bytes + P.sched_bytes + warp * P.warp_bytes;
-  float* vals = reinterpret_cast<float*>(wbase);
-  float* grads = vals + NV;
+  float* valsA[2];
+  float* gradsA[2];
+  valsA[0] = reinterpret_cast<float*>(wbase);
+  gradsA[0] = valsA[0] + NV;
+  valsA[1] = gradsA[0] + NV;
+  gradsA[1] = valsA[1] + NV;
   // padding terms read vals[0] and grads[0]: keep every entry finite from the start
-  for (int k = lane; k < 2 * NV; k += 32) vals[k] = 0.f;
-  float* GMb = grads + NV;          // 32 x NR
+  for (int k = lane; k < 4 * NV; k += 32) valsA[0][k] = 0.f;
+  float* GMb = gradsA[1] + NV;      // 32 x NR
   float* PQb = GMb + 32 * NR;       // 32 x NQ
-  float* CB = PQb + 32 * NQ;        // CBN
-  int* ZJ = reinterpret_cast<int*>(CB + CBN);
+  float* CBA[2];
+  CBA[0] = PQb + 32 * NQ;           // CBN each
+  CBA[1] = CBA[0] + CBN;
+  int* ZJ = reinterpret_cast<int*>(CBA[1] + CBN);
   __syncthreads();
   const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
 
-  for (int64_t wk = static_cast<int64_t>(blockIdx.x) * nwarps + warp; wk < P.n_work;
-       wk += static_cast<int64_t>(gridDim.x) * nwarps) {
-    const int64_t i = P.o.atom_list ? P.o.atom_list[wk] : wk;
+  // ---------------- moments of one neighborhood (eq. 3) ----------------
+  auto moments = [&](int64_t i, float* vals, float* CB) {
     const int zi = P.type[i];
     const int64_t p0 = P.nb.off[i];
     const int np = static_cast<int>(P.nb.off[i + 1] - p0);
@@ -314,7 +323,6 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
     if (MODE & F_ROWS)
       for (int e = lane; e < CBN; e += 32) CB[e] = 0.f;
     __syncwarp();
-    // ---------------- moments (eq. 3) ----------------
     for (int base = 0; base < np; base += 32) {
       const bool act = base + lane < np;
       float rx = 1.f, ry = 0.f, rz = 0.f, rr = 1.f;
@@ -326,63 +334,27 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         zj = P.type[P.nb.pj[p]];
       }
       float f[NR], df[NR];
-      radial<NR>(rr, czi + zj * NR * NQ, NQ, rmin, rcut, f, df, nullptr);
+      radial<NR, NQ>(rr, czi + zj * NR * NQ, rmin, rcut, f, df, nullptr);
       if (!act)
 #pragma unroll
         for (int mu = 0; mu < NR; ++mu) f[mu] = 0.f;
       moments_pass<NR, NU0>(rx, ry, rz, f, vals, slot_comp, lane);
     }
     __syncwarp();
-    // ---------------- forward contraction (eqs. 5-6), slab form ----------------
-    for (int r = 0; r < d.n_fround; ++r) {
-      const int4 rd = s_fround[r];
-      const uint32_t* slab = s_fslab + rd.y + lane;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      int it = 0;
-      for (; it + 4 <= rd.x; it += 4) {
-        const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32], w2 = slab[32 * it + 64], w3 = slab[32 * it + 96];
-        a0 = fmaf(coef[w0 >> 24], vals[w0 & 4095u] * vals[(w0 >> 12) & 4095u], a0);
-        a1 = fmaf(coef[w1 >> 24], vals[w1 & 4095u] * vals[(w1 >> 12) & 4095u], a1);
-        a2 = fmaf(coef[w2 >> 24], vals[w2 & 4095u] * vals[(w2 >> 12) & 4095u], a2);
-        a3 = fmaf(coef[w3 >> 24], vals[w3 & 4095u] * vals[(w3 >> 12) & 4095u], a3);
-      }
-      for (; it < rd.x; ++it) {
-        const uint32_t w0 = slab[32 * it];
-        a0 = fmaf(coef[w0 >> 24], vals[w0 & 4095u] * vals[(w0 >> 12) & 4095u], a0);
-      }
-      const int dst = s_frdst[32 * r + lane];
-      if (dst >= 0) vals[dst] = (a0 + a1) + (a2 + a3);
-      if (rd.z) __syncwarp();
-    }
-    // ---------------- site energy (eq. 2) ----------------
+  };
+
+  // ---------------- pair adjoint and outputs of one neighborhood ----------------
+  auto finish = [&](int64_t wk, int64_t i, const float* vals, const float* grads, float* CB) {
+    const int zi = P.type[i];
+    const int64_t p0 = P.nb.off[i];
+    const int np = static_cast<int>(P.nb.off[i + 1] - p0);
+    const float* czi = ctab + static_cast<size_t>(zi) * T * NR * NQ;
     if (MODE & F_EFS) {
       float acc = 0.f;
       for (int a = lane; a < d.n_lin; a += 32) acc = fmaf(d.theta_f[T + a], vals[d.basis_idx[a]], acc);
       for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
       if (lane == 0) P.o.V[i] = static_cast<double>(acc) + d.theta_d[zi];
     }
-    // ---------------- adjoint of the contraction (gather form), slab form ----------------
-    for (int r = 0; r < d.n_rround; ++r) {
-      const int4 rd = s_rround[r];
-      const uint32_t* slab = s_rslab + rd.y + lane;
-      const int x = s_rrval[32 * r + lane];
-      float a0 = x >= 0 ? s_seed[x] : 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      int it = 0;
-      for (; it + 4 <= rd.x; it += 4) {
-        const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32], w2 = slab[32 * it + 64], w3 = slab[32 * it + 96];
-        a0 = fmaf(coef[w0 >> 24], vals[w0 & 4095u] * grads[(w0 >> 12) & 4095u], a0);
-        a1 = fmaf(coef[w1 >> 24], vals[w1 & 4095u] * grads[(w1 >> 12) & 4095u], a1);
-        a2 = fmaf(coef[w2 >> 24], vals[w2 & 4095u] * grads[(w2 >> 12) & 4095u], a2);
-        a3 = fmaf(coef[w3 >> 24], vals[w3 & 4095u] * grads[(w3 >> 12) & 4095u], a3);
-      }
-      for (; it < rd.x; ++it) {
-        const uint32_t w0 = slab[32 * it];
-        a0 = fmaf(coef[w0 >> 24], vals[w0 & 4095u] * grads[(w0 >> 12) & 4095u], a0);
-      }
-      if (x >= 0) grads[x] = (a0 + a1) + (a2 + a3);
-      if (rd.z) __syncwarp();
-    }
-    // ---------------- per-pair adjoint: dV/dr_ij, virial, radial block of b_i ----------------
     double Wacc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Wacc[k] = 0.0;
@@ -397,7 +369,7 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         zj = P.type[P.nb.pj[p]];
       }
       float f[NR], df[NR], g[NR];
-      radial<NR>(rr, czi + zj * NR * NQ, NQ, rmin, rcut, f, df, (MODE & F_ROWS) ? PQb + NQ * lane : nullptr);
+      radial<NR, NQ>(rr, czi + zj * NR * NQ, rmin, rcut, f, df, (MODE & F_ROWS) ? PQb + NQ * lane : nullptr);
 #pragma unroll
       for (int mu = 0; mu < NR; ++mu) g[mu] = 0.f;
       float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -454,8 +426,7 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
     }
     if (MODE & F_ROWS) {
       const int64_t ld = P.o.rows_ld;
-      const int cb_total = T * CBN;
-      float* hi = P.o.rows_hi + wk * ld;
+      float* hi = P.o.rows_hi ? P.o.rows_hi + wk * ld : nullptr;
       float* lo = P.o.rows_lo ? P.o.rows_lo + wk * ld : nullptr;
       double* out64 = P.o.rows ? P.o.rows + wk * ld : nullptr;
       auto put = [&](int64_t k, float v) {
@@ -471,13 +442,86 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
       };
       for (int k = lane; k < T; k += 32) put(k, (k == zi) ? 1.f : 0.f);
       for (int a = lane; a < d.n_lin; a += 32) put(T + a, vals[d.basis_idx[a]]);
-      for (int e = lane; e < cb_total; e += 32) {
-        const int zblk = e / CBN;
-        put(off_c + e, (zblk == zi) ? CB[e - zblk * CBN] : 0.f);
-      }
+      for (int zblk = 0; zblk < T; ++zblk)
+        for (int e = lane; e < CBN; e += 32) put(off_c + zblk * CBN + e, (zblk == zi) ? CB[e] : 0.f);
       for (int64_t k = d.n_params + lane; k < ld; k += 32) put(k, 0.f);
     }
     __syncwarp();
+  };
+
+  for (int64_t wp = static_cast<int64_t>(blockIdx.x) * nwarps + warp; 2 * wp < P.n_work;
+       wp += static_cast<int64_t>(gridDim.x) * nwarps) {
+    const int64_t wk0 = 2 * wp, wk1 = 2 * wp + 1;
+    const bool two = wk1 < P.n_work;
+    const int64_t i0 = P.o.atom_list ? P.o.atom_list[wk0] : wk0;
+    const int64_t i1 = two ? (P.o.atom_list ? P.o.atom_list[wk1] : wk1) : i0;
+    moments(i0, valsA[0], CBA[0]);
+    if (two) moments(i1, valsA[1], CBA[1]);
+    float* v0 = valsA[0];
+    float* v1 = valsA[1];
+    float* g0 = gradsA[0];
+    float* g1 = gradsA[1];
+    // ---------------- forward contraction (eqs. 5-6): both neighborhoods per term ----------------
+    for (int r = 0; r < d.n_fround; ++r) {
+      const int4 rd = s_fround[r];
+      const uint32_t* slab = s_fslab + rd.y + lane;
+      float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+      int it = 0;
+      for (; it + 2 <= rd.x; it += 2) {
+        const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32];
+        const float c0 = coef[w0 >> 24], c1 = coef[w1 >> 24];
+        const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u, x1 = w1 & 4095u, y1 = (w1 >> 12) & 4095u;
+        a0 = fmaf(c0, v0[x0] * v0[y0], a0);
+        b0 = fmaf(c0, v1[x0] * v1[y0], b0);
+        a1 = fmaf(c1, v0[x1] * v0[y1], a1);
+        b1 = fmaf(c1, v1[x1] * v1[y1], b1);
+      }
+      if (it < rd.x) {
+        const uint32_t w0 = slab[32 * it];
+        const float c0 = coef[w0 >> 24];
+        const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u;
+        a0 = fmaf(c0, v0[x0] * v0[y0], a0);
+        b0 = fmaf(c0, v1[x0] * v1[y0], b0);
+      }
+      const int dst = s_frdst[32 * r + lane];
+      if (dst >= 0) {
+        v0[dst] = a0 + a1;
+        v1[dst] = b0 + b1;
+      }
+      if (rd.z) __syncwarp();
+    }
+    // ---------------- adjoint of the contraction (gather form): both neighborhoods ----------------
+    for (int r = 0; r < d.n_rround; ++r) {
+      const int4 rd = s_rround[r];
+      const uint32_t* slab = s_rslab + rd.y + lane;
+      const int x = s_rrval[32 * r + lane];
+      const float sd = x >= 0 ? s_seed[x] : 0.f;
+      float a0 = sd, a1 = 0.f, b0 = sd, b1 = 0.f;
+      int it = 0;
+      for (; it + 2 <= rd.x; it += 2) {
+        const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32];
+        const float c0 = coef[w0 >> 24], c1 = coef[w1 >> 24];
+        const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u, x1 = w1 & 4095u, y1 = (w1 >> 12) & 4095u;
+        a0 = fmaf(c0, v0[x0] * g0[y0], a0);
+        b0 = fmaf(c0, v1[x0] * g1[y0], b0);
+        a1 = fmaf(c1, v0[x1] * g0[y1], a1);
+        b1 = fmaf(c1, v1[x1] * g1[y1], b1);
+      }
+      if (it < rd.x) {
+        const uint32_t w0 = slab[32 * it];
+        const float c0 = coef[w0 >> 24];
+        const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u;
+        a0 = fmaf(c0, v0[x0] * g0[y0], a0);
+        b0 = fmaf(c0, v1[x0] * g1[y0], b0);
+      }
+      if (x >= 0) {
+        g0[x] = a0 + a1;
+        g1[x] = b0 + b1;
+      }
+      if (rd.z) __syncwarp();
+    }
+    finish(wk0, i0, v0, g0, CBA[0]);
+    if (two) finish(wk1, i1, v1, g1, CBA[1]);
   }
 }
 
@@ -490,7 +534,7 @@ void launch_fast(FastParams P, int nwarps, cudaStream_t s) {
   MTP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   MTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nwarps * 32, P.total));
   per_sm = std::max(per_sm, 1);
-  const int64_t need = (P.n_work + nwarps - 1) / nwarps;
+  const int64_t need = ((P.n_work + 1) / 2 + nwarps - 1) / nwarps;
   const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(nsm) * per_sm)));
   if (P.n_work == 0) return;
   ProfRegion pr((MODE & F_EFS) ? ((MODE & F_ROWS) ? "site_efs_rows" : "site_efs") : "site_rows", s);
@@ -511,7 +555,7 @@ void dispatch_mode(FastParams P, int nwarps, bool efs, bool rows, cudaStream_t s
 // the generic kernel).
 bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const SiteOutputs& o, cudaStream_t s) {
   const DevSchedule& d = m->ds;
-  if (!d.tri_pk || d.n_q > 32) return false;
+  if (!d.tri_pk || d.n_q != kNQ) return false;
   const bool efs = o.V != nullptr;
   const bool rows = o.rows != nullptr || o.rows_hi != nullptr;
   if (!efs && !rows) return false;
@@ -527,8 +571,8 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   P.NV = d.n_vals;
   P.c_bytes = (static_cast<size_t>(P.NC) * sizeof(float) + 15) & ~size_t(15);
   P.tab_bytes = ((256 + d.n_mom) * sizeof(float) + 15) & ~size_t(15);
-  P.warp_bytes = ((2 * static_cast<size_t>(P.NV) + 32 * (d.n_rad + d.n_q) + P.CBN) * sizeof(float) + 32 * sizeof(int) + 15) &
-                 ~size_t(15);
+  P.warp_bytes = ((4 * static_cast<size_t>(P.NV) + 32 * (d.n_rad + d.n_q) + 2 * P.CBN) * sizeof(float) +
+                  32 * sizeof(int) + 15) & ~size_t(15);
   // shared-memory copy of the schedule (32-bit words)
   int w = 0;
   auto take = [&](int n) { const int o = w; w += (n + 3) & ~3; return o; };
