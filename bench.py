@@ -158,6 +158,38 @@ class ClockSampler:
 # our arm
 # ------------------------------------------------------------------------------------
 
+def measure_train(api, synth, torch, steps=5, warmup=2):
+    """One training step of eq. 7 (loss + gradient) on a 512-configuration batch of 8-256 atoms
+    (fcc/bcc/hcp, random strains and species): targets from a seeded level-8 ternary teacher,
+    a level-16 ternary student, weights w_e = 1, w_f = 0.01, w_s = 0."""
+    bnp = synth.training_batch(seed=3)
+    def model_for(lev, seed):
+        desc = api.make_desc(3, lev)
+        basis = api.mtp_describe_basis(desc)
+        sz = api.mtp_describe(desc)
+        th = synth.draw_theta(seed, 3, sz["n_rad"], 8, [sum(n for _, n in l) for l, _ in basis],
+                              [len(l) for l, _ in basis], 2.0, 5.0, 42.0)
+        return api.mtp_load(desc, th)
+    teacher, student = model_for(8, 33), model_for(16, 34)
+    b = api.Batch(bnp)
+    nb = api.mtp_build_neighbors(teacher, b)
+    ref = api.mtp_energy_forces_stress(teacher, b, nb, "fp64")
+    out = {"configs": int(b.n_cfg), "atoms": int(b.n_atoms), "pairs": int(nb.size()[1]), "student_params": int(student.n_params)}
+    for prec in ("mixed", "fp64"):
+        for _ in range(warmup):
+            api.mtp_train_step(student, b, nb, ref["energy"], ref["forces"], prec=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            loss, grad = api.mtp_train_step(student, b, nb, ref["energy"], ref["forces"], prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"ms_per_step": ms, "configs_per_s": b.n_cfg / (ms / 1e3), "loss": float(loss.item())}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -325,6 +357,8 @@ def run_ours(args):
         "roofline": roof, "kernels": kernels, "gpu_launches": launches, "clocks": clk,
         "e2e": e2e,
     }
+    if not args.no_train:
+        line["train_step"] = measure_train(api, synth, torch)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line))
@@ -418,6 +452,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1024)
     ap.add_argument("--ref-sample", type=int, default=256)
     args = ap.parse_args()

@@ -1,0 +1,127 @@
+"""Parity at the benchmark scales (GPU through the C ABI vs the FP64 oracle).
+
+* fcc ternary random solid solution, 64^3 cells (1,048,576 atoms), level 20, the launch
+  configuration bench.py times (mtp_step, grade included): site energies, forces and grades
+  of sampled atoms against the oracle (which builds its own neighborhoods with its cell list
+  and evaluates every neighbor of a sampled atom, so sampled forces are exact), plus
+  properties that hold at any size (zero net force, symmetric virial).
+* B2 binary, 20^3 cells (16,000 atoms), level 16: every energy, force and the virial.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2304_13144_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api(native_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_13144_gb300 import api as A
+    return A
+
+
+def theta_for(md, seed, nbar=42.0):
+    nu_sum = [sum(nu for _, nu in labs) for labs, _ in md.basis]
+    nf = [len(labs) for labs, _ in md.basis]
+    return synth.draw_theta(seed, md.n_types, md.n_rad, md.n_q, nu_sum, nf, md.r_min, md.r_cut, nbar)
+
+
+@pytest.fixture(scope="module")
+def big(api):
+    bnp = synth.fcc_ternary(seed=4, n=64)
+    md = O.OracleModel(3, 20, 2.0, 5.0)
+    theta = theta_for(md, 44)
+    A = synth.diag_dominant(8, md.m)
+    model = api.mtp_load(api.make_desc(3, 20), theta)
+    api.mtp_set_active_set(model, torch.tensor(A, device="cuda"))
+    b = api.Batch(bnp)
+    nb = api.mtp_build_neighbors(model, b)
+    outs = {}
+    for prec in ("mixed", "fp64"):
+        o = api.mtp_step(model, b, nb, prec, threshold=2.0)
+        o["site_energy"] = api.mtp_energy_forces_stress(model, b, nb, prec)["site_energy"]
+        outs[prec] = {k: (v.cpu().numpy() if v is not None else None) for k, v in o.items()}
+    ref_nbr = O.batch_neighbors(bnp, 5.0, brute=False)
+    sample = synth.sample_atoms(123, len(bnp["type"]), 12)
+    cen = O.pair_centers(ref_nbr["off"])
+    needed = set(sample.tolist())
+    for k in sample:
+        needed.update(ref_nbr["j"][ref_nbr["off"][k]:ref_nbr["off"][k + 1]].tolist())
+    req = np.array(sorted(needed), np.int64)
+    s = O.sites(md, theta, bnp["type"], ref_nbr, req=req, want_dVdr=True, want_b=True)
+    pos_of = {int(a): q for q, a in enumerate(req)}
+    G = s["dVdr"]
+    F = np.zeros((len(sample), 3))
+    for q, k in enumerate(sample):
+        k = int(k)
+        F[q] += G[ref_nbr["off"][k]:ref_nbr["off"][k + 1]].sum(axis=0)
+        # contributions of k as a neighbor of each of its neighbors j (full list: j lists k)
+        for j in set(ref_nbr["j"][ref_nbr["off"][k]:ref_nbr["off"][k + 1]].tolist()):
+            for p in range(ref_nbr["off"][j], ref_nbr["off"][j + 1]):
+                if ref_nbr["j"][p] == k:
+                    F[q] -= G[p]
+    rows = s["b"][[pos_of[int(k)] for k in sample]]
+    gamma, am = O.grade(A, rows)
+    V = s["V"][[pos_of[int(k)] for k in sample]]
+    return {"outs": outs, "sample": sample, "V": V, "F": F, "gamma": gamma, "argmax": am, "n": len(bnp["type"])}
+
+
+def test_million_atom_site_energies_on_sampled_atoms(big):
+    k = big["sample"]
+    np.testing.assert_allclose(big["outs"]["fp64"]["site_energy"][k], big["V"], rtol=1e-10,
+                               atol=1e-10 * np.abs(big["V"]).max())
+    assert np.abs(big["outs"]["mixed"]["site_energy"][k] - big["V"]).max() <= 1e-6
+
+
+def test_million_atom_forces_on_sampled_atoms(big):
+    k = big["sample"]
+    scale = max(1.0, np.abs(big["F"]).max())
+    assert np.abs(big["outs"]["fp64"]["forces"][k] - big["F"]).max() <= 1e-10 * scale
+    assert np.abs(big["outs"]["mixed"]["forces"][k] - big["F"]).max() <= 1e-5
+
+
+def test_million_atom_grade_on_sampled_atoms(big):
+    k = big["sample"]
+    np.testing.assert_allclose(big["outs"]["fp64"]["gamma"][k], big["gamma"], rtol=1e-10)
+    assert (big["outs"]["fp64"]["argmax"][k] == big["argmax"]).all()
+    g = big["gamma"]
+    assert np.all(np.abs(big["outs"]["mixed"]["gamma"][k] - g) <= 1e-4 * np.maximum(1.0, g))
+
+
+def test_million_atom_invariants(big):
+    for prec, tol in (("fp64", 1e-9), ("mixed", 1e-3)):
+        F = big["outs"][prec]["forces"]
+        assert np.isfinite(F).all()
+        assert np.abs(F.sum(axis=0)).max() <= tol * np.abs(F).max()
+        W = big["outs"][prec]["virial"][0]
+        assert np.abs(W - W.T).max() <= (1e-9 if prec == "fp64" else 1e-5) * np.abs(W).max()
+    # flags are gamma > 2 in ascending order, identical between the FP64 count and its list
+    o = big["outs"]["fp64"]
+    nf = int(o["n_flagged"][0])
+    assert (o["flagged"][:nf] == np.nonzero(o["gamma"] > 2.0)[0]).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_b2_binary_16000_atoms_every_atom(api, prec):
+    bnp = synth.b2_binary(seed=2, n=20)
+    md = O.OracleModel(2, 16, 2.0, 5.0)
+    theta = theta_for(md, 22, nbar=58.0)
+    ref = O.efs(md, theta, bnp, O.batch_neighbors(bnp, 5.0, brute=False))
+    model = api.mtp_load(api.make_desc(2, 16), theta)
+    b = api.Batch(bnp)
+    nb = api.mtp_build_neighbors(model, b)
+    out = {k: v.cpu().numpy() for k, v in api.mtp_energy_forces_stress(model, b, nb, prec).items()}
+    n = len(bnp["type"])
+    if prec == "fp64":
+        assert np.abs(out["energy"] - ref["E"]).max() <= 1e-10 * np.abs(ref["V"]).sum()
+        assert np.abs(out["forces"] - ref["F"]).max() <= 1e-10 * np.abs(ref["F"]).max()
+        assert np.abs(out["virial"] - ref["W"]).max() <= 1e-10 * np.abs(ref["W"]).max()
+    else:
+        assert np.abs(out["energy"] - ref["E"]).max() / n <= 1e-6
+        assert np.abs(out["forces"] - ref["F"]).max() <= 1e-5
+        assert np.abs(out["virial"] - ref["W"]).max() <= 1e-5 * np.abs(ref["W"]).max()
