@@ -206,7 +206,7 @@ void upload_schedule(mtp_model* md) {
         std::vector<std::vector<uint32_t>> lists(32);
         for (int e = e0; e < e1; ++e)
           for (int u = use_ptr[rval[e]]; u < use_ptr[rval[e] + 1]; ++u) lists[e - e0].push_back(use_pk[u]);
-        const uint32_t gofs = static_cast<uint32_t>(nv);   // grads follow vals in shared memory
+        const uint32_t gofs = static_cast<uint32_t>((nv + 3) & ~3);   // grads follow vals (padded) in shared memory
         auto ord = bank_order(
             lists, L, [](uint32_t w) { return w & 4095u; }, [gofs](uint32_t w) { return gofs + ((w >> 12) & 4095u); },
             [](uint32_t w) { return w; });

@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kWarps * 32) site_kernel(SiteParams P) {
   const int64_t off_c = T + d.n_lin;
   for (int k = threadIdx.x; k < L.NC; k += blockDim.x) ctab[k] = theta[off_c + k];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;   // at most kWarps (fewer for large models)
   unsigned char* wbase = smem + L.c_bytes + warp * L.warp_bytes;
   S* vals = reinterpret_cast<S*>(wbase);
   S* grads = vals + L.NV;
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(kWarps * 32) site_kernel(SiteParams P) {
   const int np1 = nu_max + 1;
 
   double Wacc[9];
-  for (int64_t wk = static_cast<int64_t>(blockIdx.x) * kWarps + warp; wk < P.n_work;
-       wk += static_cast<int64_t>(gridDim.x) * kWarps) {
+  for (int64_t wk = static_cast<int64_t>(blockIdx.x) * nw + warp; wk < P.n_work;
+       wk += static_cast<int64_t>(gridDim.x) * nw) {
     const int64_t i = P.o.atom_list ? P.o.atom_list[wk] : wk;
     const int zi = P.type[i];
     const int64_t p0 = P.nb.off[i];
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kWarps * 32) site_kernel(SiteParams P) {
     }
     if (MODE & M_TAN) {
       // accumulate coef * b_i - d/dt b_i into this warp's row of the partial-gradient buffer
-      double* acc = P.o.grad_part + (static_cast<int64_t>(blockIdx.x) * kWarps + warp) * d.n_params;
+      double* acc = P.o.grad_part + (static_cast<int64_t>(blockIdx.x) * nw + warp) * d.n_params;
       const double coef = P.o.coef[P.nb.atom_cfg[i]];
       if (lane == 0) acc[zi] += coef;
       for (int a = lane; a < d.n_lin; a += 32) {
@@ -448,7 +449,13 @@ __global__ void __launch_bounds__(kWarps * 32) site_kernel(SiteParams P) {
 template <class S, class R, int MODE>
 void launch_sites(const SiteParams& P0, int* grid_used, cudaStream_t s) {
   SiteParams P = P0;
-  P.L = make_layout<S, R>(P.d, kWarps);
+  // as many warps per block (up to kWarps) as the per-warp value arrays leave room for
+  int warps = kWarps;
+  P.L = make_layout<S, R>(P.d, warps);
+  while (warps > 1 && P.L.total > 227 * 1024) {
+    warps >>= 1;
+    P.L = make_layout<S, R>(P.d, warps);
+  }
   if (P.L.total > 227 * 1024)
     throw Fail{MTP_ERR_UNSUPPORTED, "model too large for the per-neighborhood kernel's shared memory"};
   auto kern = site_kernel<S, R, MODE>;
@@ -457,9 +464,9 @@ void launch_sites(const SiteParams& P0, int* grid_used, cudaStream_t s) {
   int dev = 0, nsm = 0, per_sm = 0;
   MTP_CUDA(cudaGetDevice(&dev));
   MTP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  MTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, P.L.total));
+  MTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, P.L.total));
   per_sm = std::max(per_sm, 1);
-  int64_t need = (P.n_work + kWarps - 1) / kWarps;
+  int64_t need = (P.n_work + warps - 1) / warps;
   int grid = static_cast<int>(std::min<int64_t>(need, static_cast<int64_t>(nsm) * per_sm));
   grid = std::max(grid, 1);
   if (grid_used) {
@@ -469,7 +476,7 @@ void launch_sites(const SiteParams& P0, int* grid_used, cudaStream_t s) {
   if (P.n_work == 0) return;
   const char* name = (MODE & M_TAN) ? "site_tangent" : (MODE & M_EFS) ? ((MODE & M_ROWS) ? "site_efs_rows" : "site_efs") : "site_rows";
   ProfRegion pr(name, s);
-  kern<<<grid, kWarps * 32, P.L.total, s>>>(P);
+  kern<<<grid, warps * 32, P.L.total, s>>>(P);
   MTP_CUDA(cudaGetLastError());
 }
 

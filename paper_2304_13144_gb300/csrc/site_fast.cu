@@ -128,7 +128,8 @@ struct FastParams {
   const int* type;
   int64_t n_work;
   SiteOutputs o;
-  int NQ, CBN, NC, NV;
+  int NQ, CBN, NC, NV;  // NV: per-neighborhood value slots, padded to a multiple of 4
+  bool row_stage;       // rows are assembled in the adjoint buffer and written as float4
   size_t c_bytes, tab_bytes, sched_bytes, warp_bytes, total;
   // word offsets of the schedule arrays inside the shared-memory copy
   int o_fslab, o_fround, o_frdst, o_rslab, o_rround, o_rrval, o_seed;
@@ -355,9 +356,9 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
       for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
       if (lane == 0) P.o.V[i] = static_cast<double>(acc) + d.theta_d[zi];
     }
-    double Wacc[9];
+    float Wl[9];   // this lane's pairs (at most a few terms) in FP32; the warp sum below in FP64
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Wacc[k] = 0.0;
+    for (int k = 0; k < 9; ++k) Wl[k] = 0.f;
     for (int base = 0; base < np; base += 32) {
       const bool act = base + lane < np;
       float rx = 1.f, ry = 0.f, rz = 0.f, rr = 1.f;
@@ -392,11 +393,11 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         Gout[3 * p + 0] = gx;
         Gout[3 * p + 1] = gy;
         Gout[3 * p + 2] = gz;
-        const double g3[3] = {gx, gy, gz}, r3[3] = {rx, ry, rz};
+        const float g3[3] = {gx, gy, gz}, r3[3] = {rx, ry, rz};
 #pragma unroll
         for (int a2 = 0; a2 < 3; ++a2)
 #pragma unroll
-          for (int b2 = 0; b2 < 3; ++b2) Wacc[3 * a2 + b2] -= g3[a2] * r3[b2];
+          for (int b2 = 0; b2 < 3; ++b2) Wl[3 * a2 + b2] = fmaf(-g3[a2], r3[b2], Wl[3 * a2 + b2]);
       }
       __syncwarp();
       if (MODE & F_ROWS) {
@@ -416,15 +417,12 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
     if (MODE & F_EFS) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        double v = Wacc[k];
+        double v = static_cast<double>(Wl[k]);
         for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-        Wacc[k] = v;
+        if (lane == 0) P.o.Wat[9 * i + k] = v;
       }
-      if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) P.o.Wat[9 * i + k] = Wacc[k];
     }
-    if (MODE & F_ROWS) {
+    if ((MODE & F_ROWS) && !P.row_stage) {
       const int64_t ld = P.o.rows_ld;
       float* hi = P.o.rows_hi ? P.o.rows_hi + wk * ld : nullptr;
       float* lo = P.o.rows_lo ? P.o.rows_lo + wk * ld : nullptr;
@@ -445,6 +443,38 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
       for (int zblk = 0; zblk < T; ++zblk)
         for (int e = lane; e < CBN; e += 32) put(off_c + zblk * CBN + e, (zblk == zi) ? CB[e] : 0.f);
       for (int64_t k = d.n_params + lane; k < ld; k += 32) put(k, 0.f);
+    }
+    if ((MODE & F_ROWS) && P.row_stage) {
+      // assemble b_i (eq. 9) in the adjoint buffer -- its values are no longer needed -- and
+      // write it with 16-byte stores
+      const int64_t ld = P.o.rows_ld;
+      float* row = const_cast<float*>(grads);
+      __syncwarp();
+      for (int k = lane; k < ld; k += 32) row[k] = 0.f;
+      __syncwarp();
+      if (lane == 0) row[zi] = 1.f;
+      for (int a = lane; a < d.n_lin; a += 32) row[T + a] = vals[d.basis_idx[a]];
+      for (int e = lane; e < CBN; e += 32) row[off_c + zi * CBN + e] = CB[e];
+      __syncwarp();
+      if (P.o.rows) {
+        double* out64 = P.o.rows + wk * ld;
+        for (int k = lane; k < d.n_params; k += 32) out64[k] = row[k];
+      }
+      if (P.o.rows_hi) {
+        float4* hi = reinterpret_cast<float4*>(P.o.rows_hi + wk * ld);
+        float4* lo = P.o.rows_lo ? reinterpret_cast<float4*>(P.o.rows_lo + wk * ld) : nullptr;
+        const float4* src = reinterpret_cast<const float4*>(row);
+        for (int k = lane; k < ld / 4; k += 32) {
+          const float4 v = src[k];
+          if (lo) {
+            const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+            hi[k] = h;
+            lo[k] = make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+          } else {
+            hi[k] = v;
+          }
+        }
+      }
     }
     __syncwarp();
   };
@@ -568,7 +598,8 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   P.NQ = d.n_q;
   P.CBN = d.n_types * d.n_rad * d.n_q;
   P.NC = d.n_types * P.CBN;
-  P.NV = d.n_vals;
+  P.NV = (d.n_vals + 3) & ~3;
+  P.row_stage = o.rows_ld > 0 && o.rows_ld <= P.NV && (o.rows_ld & 3) == 0;
   P.c_bytes = (static_cast<size_t>(P.NC) * sizeof(float) + 15) & ~size_t(15);
   P.tab_bytes = ((256 + d.n_mom) * sizeof(float) + 15) & ~size_t(15);
   P.warp_bytes = ((4 * static_cast<size_t>(P.NV) + 32 * (d.n_rad + d.n_q) + 2 * P.CBN) * sizeof(float) +
