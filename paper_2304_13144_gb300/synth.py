@@ -107,6 +107,99 @@ def fcc_ternary(seed=4, n=64, a=3.6, sigma=0.1):
     return single(pos, types, cell)
 
 
+def liquid_rsa(seed=5, n_atoms=2_097_152, density=0.085, d_min=1.8, n_types=4, tiles=1):
+    """Liquid-like configuration: random sequential addition of points, uniform in a periodic
+    cube of volume n_atoms/density, each new point kept only if it is at least d_min from every
+    point kept before; species uniform over n_types, drawn for every atom.
+
+    With tiles = t > 1 the addition fills a cube of n_atoms/t^3 points and the cube is repeated
+    t x t x t times (its periodic boundary makes the copy seamless): the density, the minimum
+    distance and every neighborhood's statistics are those of the single cube, at a fraction of
+    the generation time.  n_atoms must then be a multiple of t^3.
+
+    Candidates are drawn in batches.  A grid of cells no wider than d_min/sqrt(3) holds at most
+    one point per cell; a candidate is tested against the kept points in the 5x5x5 cells around
+    its own, then against earlier candidates of its batch (a candidate that meets an earlier one
+    within d_min is dropped, even if that earlier one is dropped too), which keeps every pair of
+    kept points at least d_min apart."""
+    if n_atoms % (tiles ** 3):
+        raise ValueError("n_atoms must be a multiple of tiles^3")
+    g = rng(seed)
+    n_total, n_atoms = n_atoms, n_atoms // tiles ** 3
+    L = (n_atoms / density) ** (1.0 / 3.0)
+    M = int(math.ceil(L / (d_min / math.sqrt(3.0))))
+    cs = L / M
+    grid = np.full(M * M * M, -1, np.int64)
+    pos = np.empty((n_atoms, 3))
+    n = 0
+    offs = np.stack(np.meshgrid(*(np.arange(-2, 3),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    d2 = d_min * d_min
+    acc = 1.0
+
+    def cells(x):
+        c = np.minimum((x / cs).astype(np.int64), M - 1)
+        return c
+
+    def flat(c):
+        c = np.mod(c, M)
+        return (c[:, 0] * M + c[:, 1]) * M + c[:, 2]
+
+    def conflicts(x, c, table, pts, idx_limit=None):
+        bad = np.zeros(len(x), bool)
+        for o in offs:
+            k = table[flat(c + o)]
+            hit = k >= 0
+            if idx_limit is not None:
+                hit &= k < idx_limit
+            if not hit.any():
+                continue
+            h = np.nonzero(hit)[0]
+            d = x[h] - pts[k[h]]
+            d -= L * np.round(d / L)
+            bad[h[(d * d).sum(1) < d2]] = True
+        return bad
+
+    while n < n_atoms:
+        need = n_atoms - n
+        K = int(min(4_000_000, max(100_000, 2.0 * need / max(acc, 0.02))))
+        x = g.uniform(0.0, L, (K, 3))
+        c = cells(x)
+        ok = ~conflicts(x, c, grid, pos) if n else np.ones(K, bool)
+        x, c = x[ok], c[ok]
+        f = flat(c)
+        # earlier candidates of the batch: first one per cell, then the 5x5x5 neighbourhood
+        _, first = np.unique(f, return_index=True)
+        keep = np.zeros(len(x), bool)
+        keep[first] = True
+        x, c, f = x[keep], c[keep], f[keep]
+        order = np.arange(len(x))
+        tmp = np.full(M * M * M, -1, np.int64)
+        tmp[f] = order
+        bad = np.zeros(len(x), bool)
+        for o in offs:
+            if not o.any():
+                continue
+            k = tmp[flat(c + o)]
+            hit = (k >= 0) & (k < order)
+            if not hit.any():
+                continue
+            h = np.nonzero(hit)[0]
+            d = x[h] - x[k[h]]
+            d -= L * np.round(d / L)
+            bad[h[(d * d).sum(1) < d2]] = True
+        x, f = x[~bad], f[~bad]
+        take = min(len(x), need)
+        pos[n:n + take] = x[:take]
+        grid[f[:take]] = np.arange(n, n + take)
+        n += take
+        acc = max(take / K, 1e-3)
+    if tiles > 1:
+        t = np.stack(np.meshgrid(*(np.arange(tiles),) * 3, indexing="ij"), -1).reshape(-1, 3)
+        pos = (pos[None, :, :] + L * t[:, None, :]).reshape(-1, 3)
+    types = g.integers(0, n_types, n_total).astype(np.int32)
+    return single(pos, types, np.eye(3) * (L * tiles))
+
+
 def _realisable(target, per_cell):
     best = None
     for nx in range(1, 9):
