@@ -203,6 +203,25 @@ mtp_status mtp_grade(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nb
                      mtp_precision prec, double threshold, double* gamma, int32_t* argmax,
                      int32_t* flagged, int64_t* n_flagged, void* stream);
 
+/* Copy of the current active-set matrix A (DEVICE out, m x m FP64, row-major; row j is the
+ * parameter row of the j-th active neighborhood).  Requires mtp_set_active_set. */
+mtp_status mtp_get_active_set(const mtp_model* model, double* A, void* stream);
+
+/* MaxVol update of the active set (Section II.D, D-optimality: the active set is the m x m
+ * matrix of maximal |det A|).  With C = B A^-1 for the candidate rows B, replacing active row
+ * j by candidate row i multiplies |det A| by |C_ij|; the update repeatedly makes the swap at
+ * the largest |C_ij| (ties: lowest i, then lowest j) while it exceeds 1 + eps, following C and
+ * A^-1 by rank-one corrections in FP64, then forms A^-1 afresh from the final A by LU.  A row
+ * swapped out is dropped (it is not a candidate); a candidate enters at most once.
+ *   B        DEVICE [n x m] FP64 candidate rows (e.g. mtp_param_rows of flagged atoms)
+ *   eps      >= 0; max_swaps >= 0 bounds the number of swaps
+ *   source   DEVICE [m] int64 out, or NULL: -1 for a kept active row, else the index in B of
+ *            the candidate now in its place
+ *   n_swaps  HOST out, or NULL: swaps made
+ * Requires mtp_set_active_set; MTP_ERR_SINGULAR if the final A cannot be factorised. */
+mtp_status mtp_maxvol(mtp_model* model, const double* B, int64_t n, double eps, int64_t max_swaps,
+                      int64_t* source, int64_t* n_swaps, void* stream);
+
 /* One step of MD with extrapolation control (Section III.B): energies, forces, virial and
  * the grade from a single pass over the neighborhoods.  Arguments as in
  * mtp_energy_forces_stress and mtp_grade; gamma may be NULL to skip the grade. */

@@ -63,6 +63,8 @@ _SIGS = {
     "mtp_set_params": (ctypes.c_int, [_P, _P, _I64]),
     "mtp_set_active_set": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mtp_get_active_inverse": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_get_active_set": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_maxvol": (ctypes.c_int, [_P, _P, _I64, _D, _I64, _P, _P, _P]),
     "mtp_build_neighbors": (ctypes.c_int, [_P, _P, _P, _P]),
     "mtp_free_nbr": (None, [_P]),
     "mtp_nbr_size": (ctypes.c_int, [_P, _P, _P]),
@@ -261,6 +263,25 @@ def mtp_get_active_inverse(model: Model, stream=None):
     out = torch.empty((m, m), dtype=torch.float64, device="cuda")
     _check(lib().mtp_get_active_inverse(model.h, _ptr(out), _stream(stream)))
     return out
+
+
+def mtp_get_active_set(model: Model, stream=None):
+    m = model.n_params
+    out = torch.empty((m, m), dtype=torch.float64, device="cuda")
+    _check(lib().mtp_get_active_set(model.h, _ptr(out), _stream(stream)))
+    return out
+
+
+def mtp_maxvol(model: Model, B: torch.Tensor, eps=1e-3, max_swaps=1_000_000, stream=None):
+    """MaxVol update of the model's active set with candidate rows B (n x m): returns
+    (source[m] int64 device tensor, number of swaps)."""
+    B = B.to(device="cuda", dtype=torch.float64).contiguous()
+    n = int(B.shape[0]) if B.dim() == 2 else 0
+    source = torch.empty(model.n_params, dtype=torch.int64, device="cuda")
+    swaps = ctypes.c_int64()
+    _check(lib().mtp_maxvol(model.h, _ptr(B) if n else None, n, float(eps), int(max_swaps), _ptr(source),
+                            ctypes.byref(swaps), _stream(stream)))
+    return source, swaps.value
 
 
 def mtp_build_neighbors(model: Model, batch: Batch, nbr: Neighbors | None = None, stream=None) -> Neighbors:

@@ -129,11 +129,16 @@ void upload_schedule(mtp_model* md) {
     tri_ab[t] = static_cast<uint32_t>(S.tri_a[t]) | (static_cast<uint32_t>(S.tri_b[t]) << 16);
     tri_cf[t] = static_cast<float>(S.tri_c[t]);
   }
-  // uses (gather form of the adjoint)
+  // uses (gather form of the adjoint): d(c v_a v_b)/dv_a = c v_b, one entry per operand; a
+  // square (a == b) gives the single entry 2 c v_a
   std::vector<std::vector<std::pair<uint32_t, double>>> uses(nv);
   for (int d = 0; d < nd; ++d)
     for (int t = S.dst_ptr[d]; t < S.dst_ptr[d + 1]; ++t) {
       const uint32_t dst = static_cast<uint32_t>(nm + d);
+      if (S.tri_a[t] == S.tri_b[t]) {
+        uses[S.tri_a[t]].push_back({static_cast<uint32_t>(S.tri_a[t]) | (dst << 16), 2.0 * S.tri_c[t]});
+        continue;
+      }
       uses[S.tri_a[t]].push_back({static_cast<uint32_t>(S.tri_b[t]) | (dst << 16), S.tri_c[t]});
       uses[S.tri_b[t]].push_back({static_cast<uint32_t>(S.tri_a[t]) | (dst << 16), S.tri_c[t]});
     }
@@ -161,6 +166,7 @@ void upload_schedule(mtp_model* md) {
   }
   // packed words for the specialised kernel
   std::vector<double> coefs(S.tri_c.begin(), S.tri_c.end());
+  coefs.insert(coefs.end(), use_cd.begin(), use_cd.end());
   std::sort(coefs.begin(), coefs.end());
   coefs.erase(std::unique(coefs.begin(), coefs.end()), coefs.end());
   const bool packable = nv <= 4096 && coefs.size() <= 255;
@@ -538,7 +544,31 @@ mtp_status mtp_set_active_set(mtp_model* md, const double* A, int64_t m, void* s
     check_model(md);
     if (!A || m != md->sched.n_params) throw Fail{MTP_ERR_ARG, "active-set matrix must be m x m"};
     md->have_ainv = false;
-    run_lu_inverse(md, A, m, as_stream(stream));
+    cudaStream_t s = as_stream(stream);
+    md->a_d.ensure(m * m * sizeof(double), s);
+    MTP_CUDA(cudaMemcpyAsync(md->a_d.p, A, m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    run_lu_inverse(md, md->a_d.as<double>(), m, s);
+  });
+}
+
+mtp_status mtp_get_active_set(const mtp_model* md, double* A, void* stream) {
+  return guarded([&] {
+    check_model(md);
+    if (!md->have_ainv || !A) throw Fail{MTP_ERR_ARG, "no active set or null output"};
+    MTP_CUDA(cudaMemcpyAsync(A, md->a_d.p, md->m_active * md->m_active * sizeof(double), cudaMemcpyDeviceToDevice,
+                             as_stream(stream)));
+  });
+}
+
+mtp_status mtp_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_t max_swaps, int64_t* source,
+                      int64_t* n_swaps, void* stream) {
+  return guarded([&] {
+    check_model(md);
+    if (!md->have_ainv) throw Fail{MTP_ERR_ARG, "no active set (call mtp_set_active_set)"};
+    if (n < 0 || (n > 0 && !B)) throw Fail{MTP_ERR_ARG, "null or negative candidate rows"};
+    if (!(eps >= 0.0) || max_swaps < 0) throw Fail{MTP_ERR_ARG, "eps and max_swaps must be non-negative"};
+    const int64_t k = run_maxvol(md, B, n, eps, max_swaps, source, as_stream(stream));
+    if (n_swaps) *n_swaps = k;
   });
 }
 

@@ -153,6 +153,7 @@ struct mtp_model {
   // active set
   bool have_ainv = false;
   int64_t m_active = 0;
+  mtp::DevBuf a_d;             // m x m FP64 active-set matrix (rows = active neighborhoods)
   mtp::DevBuf ainv_d;          // m x m FP64
   mtp::DevBuf ainv_f;          // padded FP32 (hi) and (lo) for the mixed grade
   int64_t ainv_ld = 0;
@@ -212,6 +213,8 @@ void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStre
 void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, double* E, double* W,
                      DevBuf& tmp, cudaStream_t s);
 void run_lu_inverse(mtp_model* m, const double* A, int64_t n, cudaStream_t s);
+int64_t run_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_t max_swaps, int64_t* source,
+                   cudaStream_t s);
 void run_grade(mtp_model* m, int64_t N, bool fp64, const double* rows, const float* rows_hi,
                const float* rows_lo, int64_t ld, double* gamma, int32_t* argmax, cudaStream_t s);
 void run_flag(int64_t N, const double* gamma, double threshold, int32_t* flagged, int64_t* n_flagged,

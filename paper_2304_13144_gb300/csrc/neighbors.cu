@@ -187,8 +187,10 @@ __device__ __forceinline__ int decide(const NbrArgs& A, const DevCfg& C, int64_t
 
 template <bool FILL>
 __global__ void k_pairs(NbrArgs A) {
-  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= A.n_atoms) return;
+  // threads take the atoms in bin order, so that a warp's atoms scan the same or adjacent bins
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= A.n_atoms) return;
+  const int64_t i = A.bin_atoms[t];
   const int k = A.atom_cfg[i];
   const DevCfg& C = A.cfg[k];
   const long long bin = A.atom_bin[i] - C.bin_base;
@@ -236,24 +238,26 @@ __global__ void k_pairs(NbrArgs A) {
   else if (count != out_end - A.off[i]) atomicOr(A.err, ERRF_CAPACITY);
 }
 
-__global__ void k_reverse(NbrArgs A, long long n_pairs) {
-  long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (p >= n_pairs) return;
-  // owner i of pair p: binary search over off
-  long long lo = 0, hi = A.n_atoms - 1;
-  while (lo < hi) {
-    long long mid = (lo + hi + 1) >> 1;
-    if (A.off[mid] <= p) lo = mid; else hi = mid - 1;
+// prev[p] = index of the reverse pair (j -> i, -image) of pair p = (i -> j, image): one warp
+// per atom i (its pairs over the lanes), each lane scanning j's list.
+__global__ void k_reverse(NbrArgs A) {
+  const int lane = threadIdx.x & 31;
+  const long long wpb = blockDim.x >> 5;
+  const long long nw = static_cast<long long>(gridDim.x) * wpb;
+  for (long long i = blockIdx.x * wpb + (threadIdx.x >> 5); i < A.n_atoms; i += nw) {
+    const long long p1 = A.off[i + 1];
+    for (long long p = A.off[i] + lane; p < p1; p += 32) {
+      const int j = A.pj[p];
+      const int img = A.pimg[p];
+      const int want = pack_img(-unpack_img(img, 0), -unpack_img(img, 1), -unpack_img(img, 2));
+      int found = -1;
+      const long long q1 = A.off[j + 1];
+      for (long long q = A.off[j]; q < q1; ++q)
+        if (A.pj[q] == static_cast<int>(i) && A.pimg[q] == want) { found = static_cast<int>(q); break; }
+      if (found < 0) atomicOr(A.err, ERRF_REVERSE);
+      A.prev[p] = found < 0 ? static_cast<int>(p) : found;
+    }
   }
-  const int i = static_cast<int>(lo);
-  const int j = A.pj[p];
-  const int img = A.pimg[p];
-  const int want = pack_img(-unpack_img(img, 0), -unpack_img(img, 1), -unpack_img(img, 2));
-  int found = -1;
-  for (long long q = A.off[j]; q < A.off[j + 1]; ++q)
-    if (A.pj[q] == i && A.pimg[q] == want) { found = static_cast<int>(q); break; }
-  if (found < 0) atomicOr(A.err, ERRF_REVERSE);
-  A.prev[p] = found < 0 ? static_cast<int>(p) : found;
 }
 
 template <class T>
@@ -444,7 +448,7 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   k_pairs<true><<<blocks_for(N, 128), 128, 0, s>>>(A);
   MTP_CUDA(cudaGetLastError());
   if (total > 0) {
-    k_reverse<<<blocks_for(total, 256), 256, 0, s>>>(A, total);
+    k_reverse<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
     MTP_CUDA(cudaGetLastError());
   }
   delete pr2;
