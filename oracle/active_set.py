@@ -33,3 +33,36 @@ def maxvol(A, B, eps=1e-3, max_swaps=10_000):
         source[j] = i
         swaps += 1
     return A, source, swaps
+
+
+# ------------------------------------------------------------------------------------
+# configuration-level grades and the learning-on-the-fly thresholds (Sections II.D-II.E)
+# ------------------------------------------------------------------------------------
+
+def config_rows(model, theta, batch, nbr=None):
+    """b(cfg_k) = dE_k/dtheta = sum_{i in k} b_i (eq. 1 differentiated with eq. 9)."""
+    from . import oracle as O
+    if nbr is None:
+        nbr = O.batch_neighbors(batch, model.r_cut)
+    rows = O.site_rows(model, theta, batch["type"], nbr)
+    off = batch["atom_offset"]
+    return np.stack([rows[off[k]:off[k + 1]].sum(axis=0) for k in range(len(off) - 1)])
+
+
+def config_grade(A, rows_cfg):
+    """gamma(cfg) = max_j |(b(cfg) A^-1)_j| against a configuration-mode active set A."""
+    from . import oracle as O
+    return O.grade(A, rows_cfg)
+
+
+def neighborhood_config_grade(gamma_atoms, atom_offset):
+    """gamma(cfg) = max over the configuration's neighborhoods of gamma_i (0 for an empty one)."""
+    return np.array([max(gamma_atoms[atom_offset[k]:atom_offset[k + 1]], default=0.0)
+                     for k in range(len(atom_offset) - 1)])
+
+
+def classify(gamma, gamma_save, gamma_break):
+    """0: gamma <= gamma_save (continue); 1: gamma_save < gamma <= gamma_break (save the
+    configuration and continue); 2: gamma > gamma_break (stop).  Strict comparisons."""
+    gamma = np.asarray(gamma)
+    return (gamma > gamma_save).astype(np.int32) + (gamma > gamma_break).astype(np.int32)

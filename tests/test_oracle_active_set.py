@@ -70,3 +70,49 @@ def test_maxvol_no_candidates_or_already_maximal():
     assert ns == 0 and (src < 0).all()
     A, src, ns = AS.maxvol(A0, B)      # tiny candidates never beat the active rows
     assert ns == 0 and np.array_equal(A, A0)
+
+
+# ---------------------------------------------------------------------------------
+# configuration-level grades
+# ---------------------------------------------------------------------------------
+
+def _small_model_and_batch():
+    from oracle import oracle as O
+    md = O.OracleModel(2, 8, 2.0, 5.0)
+    nu_sum = [sum(nu for _, nu in labs) for labs, _ in md.basis]
+    nf = [len(labs) for labs, _ in md.basis]
+    theta = synth.draw_theta(41, 2, md.n_rad, md.n_q, nu_sum, nf, 2.0, 5.0, 40.0)
+    batch = synth.training_batch(seed=42, n_cfg=3, n_types=2, lo=4, hi=20)
+    return O, md, theta, batch
+
+
+def test_config_rows_are_energy_gradients():
+    """b(cfg_k) . d = dE_k/dtheta . d by central differences of the oracle's energies."""
+    O, md, theta, batch = _small_model_and_batch()
+    nbr = O.batch_neighbors(batch, md.r_cut)
+    R = AS.config_rows(md, theta, batch, nbr)
+    g = synth.rng(43)
+    for _ in range(3):
+        d = g.normal(size=theta.size) * np.abs(theta).clip(1e-3)
+        h = 1e-4
+        Ep = O.efs(md, theta + h * d, batch, nbr)["E"]
+        Em = O.efs(md, theta - h * d, batch, nbr)["E"]
+        np.testing.assert_allclose(R @ d, (Ep - Em) / (2 * h), rtol=1e-6, atol=1e-9)
+
+
+def test_config_grade_of_an_active_configuration_is_one():
+    """A configuration whose row is in the active set has gamma(cfg) = 1 exactly (its
+    coefficients are a unit vector)."""
+    g = synth.rng(44)
+    A = g.normal(size=(6, 6)) + 3 * np.eye(6)
+    gam, am = AS.config_grade(A, A[[2, 4]])
+    np.testing.assert_allclose(gam, 1.0, rtol=1e-12)
+    assert list(am) == [2, 4]
+
+
+def test_neighborhood_config_grade_and_classes():
+    gam = np.array([0.5, 3.0, 1.2, 11.0, 2.0, 10.0])
+    off = np.array([0, 2, 2, 4, 6])
+    assert list(AS.neighborhood_config_grade(gam, off)) == [3.0, 0.0, 11.0, 10.0]
+    cls = AS.classify(np.array([0.5, 2.0, 2.0000001, 10.0, 10.5]), 2.0, 10.0)
+    assert list(cls) == [0, 0, 1, 1, 2]
