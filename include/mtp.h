@@ -222,6 +222,31 @@ mtp_status mtp_get_active_set(const mtp_model* model, double* A, void* stream);
 mtp_status mtp_maxvol(mtp_model* model, const double* B, int64_t n, double eps, int64_t max_swaps,
                       int64_t* source, int64_t* n_swaps, void* stream);
 
+/* Configuration rows b(cfg_k) = dE_k/dtheta = sum_{i in k} b_i (eq. 1 with eq. 9): DEVICE
+ * rows[n_cfg x m] FP64 out (sums over a configuration's atoms in a fixed order). */
+mtp_status mtp_config_rows(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                           mtp_precision prec, double* rows, void* stream);
+
+typedef enum {
+  MTP_GRADE_NEIGHBORHOOD = 0,   /* gamma(cfg) = max over the configuration's atoms of gamma_i */
+  MTP_GRADE_CONFIGURATION = 1   /* gamma(cfg) = max_j |(b(cfg) A^-1)_j|, A from configuration rows */
+} mtp_grade_mode;
+
+/* Configuration grades and the learning-on-the-fly classes (Sections II.D-II.E).
+ *   gamma_cfg  DEVICE [n_cfg] FP64 out
+ *   worst      DEVICE [n_cfg] int64 out, or NULL: neighborhood mode -> the atom with the
+ *              largest gamma_i (lowest index on ties, -1 for an empty configuration);
+ *              configuration mode -> the active row j attaining the maximum
+ *   cls        DEVICE [n_cfg] int32 out, or NULL: 0 if gamma <= gamma_save (continue),
+ *              1 if gamma_save < gamma <= gamma_break (save), 2 if gamma > gamma_break (stop)
+ * The active set must match the mode (rows of neighborhoods or of configurations).  The
+ * configuration-mode product is formed in FP64; prec sets the arithmetic of the rows (and of
+ * the per-atom grade in neighborhood mode). */
+mtp_status mtp_config_grade(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                            mtp_precision prec, mtp_grade_mode mode, double gamma_save,
+                            double gamma_break, double* gamma_cfg, int64_t* worst, int32_t* cls,
+                            void* stream);
+
 /* One step of MD with extrapolation control (Section III.B): energies, forces, virial and
  * the grade from a single pass over the neighborhoods.  Arguments as in
  * mtp_energy_forces_stress and mtp_grade; gamma may be NULL to skip the grade. */

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmtp.so")
 
 MTP_FP64 = 0
 MTP_MIXED = 1
+MTP_GRADE_NEIGHBORHOOD = 0
+MTP_GRADE_CONFIGURATION = 1
 STATUS = {0: "MTP_OK", 1: "MTP_ERR_ARG", 2: "MTP_ERR_CUDA", 3: "MTP_ERR_CAPACITY", 4: "MTP_ERR_SINGULAR",
           5: "MTP_ERR_GEOMETRY", 6: "MTP_ERR_NUMERIC", 7: "MTP_ERR_UNSUPPORTED"}
 
@@ -64,6 +66,8 @@ _SIGS = {
     "mtp_set_active_set": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mtp_get_active_inverse": (ctypes.c_int, [_P, _P, _P]),
     "mtp_get_active_set": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_config_rows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
+    "mtp_config_grade": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _D, _D, _P, _P, _P, _P]),
     "mtp_maxvol": (ctypes.c_int, [_P, _P, _I64, _D, _I64, _P, _P, _P]),
     "mtp_build_neighbors": (ctypes.c_int, [_P, _P, _P, _P]),
     "mtp_free_nbr": (None, [_P]),
@@ -378,6 +382,26 @@ def mtp_step(model, batch, nbr, prec="mixed", threshold=2.0, out=None, grade=Tru
                           float(threshold), _ptr(g), _ptr(out.get("argmax")), _ptr(out.get("flagged")),
                           _ptr(out.get("n_flagged")), _stream(stream)))
     return out
+
+
+def mtp_config_rows(model, batch, nbr, prec="fp64", stream=None):
+    rows = torch.empty((batch.n_cfg, model.n_params), dtype=torch.float64, device="cuda")
+    _check(lib().mtp_config_rows(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(rows), _stream(stream)))
+    return rows
+
+
+def mtp_config_grade(model, batch, nbr, prec="fp64", mode="neighborhood", gamma_save=2.0, gamma_break=10.0,
+                     stream=None):
+    """Per-configuration grade, the worst atom (neighborhood mode) or active row (configuration
+    mode), and the class 0 continue / 1 save / 2 stop."""
+    md = {"neighborhood": MTP_GRADE_NEIGHBORHOOD, "configuration": MTP_GRADE_CONFIGURATION}[mode]
+    K = batch.n_cfg
+    gamma = torch.empty(K, dtype=torch.float64, device="cuda")
+    worst = torch.empty(K, dtype=torch.int64, device="cuda")
+    cls = torch.empty(K, dtype=torch.int32, device="cuda")
+    _check(lib().mtp_config_grade(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), md, float(gamma_save),
+                                  float(gamma_break), _ptr(gamma), _ptr(worst), _ptr(cls), _stream(stream)))
+    return {"gamma": gamma, "worst": worst, "class": cls}
 
 
 def mtp_extract_neighborhoods(nbr, batch, idx: torch.Tensor, capacity=None, stream=None):

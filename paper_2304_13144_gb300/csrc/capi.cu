@@ -682,6 +682,59 @@ mtp_status mtp_grade(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_p
   });
 }
 
+mtp_status mtp_config_rows(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec, double* rows,
+                           void* stream) {
+  return guarded([&] {
+    check_run(md, b, nb);
+    if (prec != MTP_FP64 && prec != MTP_MIXED) throw Fail{MTP_ERR_ARG, "unknown precision"};
+    if (!rows) throw Fail{MTP_ERR_ARG, "null rows"};
+    cudaStream_t s = as_stream(stream);
+    const int64_t m = md->sched.n_params, N = nb->n_atoms;
+    md->ws_rows.ensure(std::max<int64_t>(N, 1) * m * sizeof(double), s);
+    SiteOutputs o;
+    o.rows = md->ws_rows.as<double>();
+    o.rows_ld = m;
+    run_sites(md, b, nb, prec == MTP_FP64, o, false, nullptr, s);
+    run_config_row_sums(nb, md->ws_rows.as<double>(), m, rows, md->ws_red, s);
+  });
+}
+
+mtp_status mtp_config_grade(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec,
+                            mtp_grade_mode mode, double gamma_save, double gamma_break, double* gamma_cfg,
+                            int64_t* worst, int32_t* cls, void* stream) {
+  return guarded([&] {
+    check_run(md, b, nb);
+    if (!gamma_cfg) throw Fail{MTP_ERR_ARG, "null gamma_cfg"};
+    if (mode != MTP_GRADE_NEIGHBORHOOD && mode != MTP_GRADE_CONFIGURATION) throw Fail{MTP_ERR_ARG, "unknown mode"};
+    if (!md->have_ainv) throw Fail{MTP_ERR_ARG, "no active set (call mtp_set_active_set)"};
+    cudaStream_t s = as_stream(stream);
+    const int64_t m = md->sched.n_params, K = nb->n_cfg;
+    DevBuf work;
+    if (mode == MTP_GRADE_NEIGHBORHOOD) {
+      work.ensure(std::max<int64_t>(nb->n_atoms, 1) * sizeof(double), s);
+      efs_and_grade(md, b, nb, prec, nullptr, nullptr, nullptr, nullptr, 0.0, work.as<double>(), nullptr, nullptr,
+                    nullptr, s);
+      run_config_gamma_max(nb, work.as<double>(), gamma_cfg, worst, md->ws_misc, s);
+    } else {
+      if (prec != MTP_FP64 && prec != MTP_MIXED) throw Fail{MTP_ERR_ARG, "unknown precision"};
+      work.ensure(std::max<int64_t>(K, 1) * (m * sizeof(double) + sizeof(int32_t)) + 64, s);
+      double* rc = work.as<double>();
+      int32_t* am = reinterpret_cast<int32_t*>(rc + std::max<int64_t>(K, 1) * m);
+      const int64_t N = nb->n_atoms;
+      md->ws_rows.ensure(std::max<int64_t>(N, 1) * m * sizeof(double), s);
+      SiteOutputs o;
+      o.rows = md->ws_rows.as<double>();
+      o.rows_ld = m;
+      run_sites(md, b, nb, prec == MTP_FP64, o, false, nullptr, s);
+      run_config_row_sums(nb, md->ws_rows.as<double>(), m, rc, md->ws_red, s);
+      run_grade_simt(md, K, true, rc, nullptr, m, gamma_cfg, am, s);
+      if (worst) run_widen_argmax(am, K, worst, s);
+    }
+    if (cls) run_classify(gamma_cfg, K, gamma_save, gamma_break, cls, s);
+    MTP_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
 mtp_status mtp_step(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec, double* energy,
                     double* site_energy, double* forces, double* virial, double threshold, double* gamma,
                     int32_t* argmax, int32_t* flagged, int64_t* n_flagged, void* stream) {

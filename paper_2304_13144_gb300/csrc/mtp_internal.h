@@ -213,6 +213,11 @@ void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStre
 void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, double* E, double* W,
                      DevBuf& tmp, cudaStream_t s);
 void run_lu_inverse(mtp_model* m, const double* A, int64_t n, cudaStream_t s);
+void run_config_row_sums(const mtp_nbr* nb, const double* rows, int64_t m, double* out, DevBuf& tmp, cudaStream_t s);
+void run_config_gamma_max(const mtp_nbr* nb, const double* gamma, double* gamma_cfg, int64_t* worst, DevBuf& tmp,
+                          cudaStream_t s);
+void run_classify(const double* gamma, int64_t n, double g_save, double g_break, int32_t* cls, cudaStream_t s);
+void run_widen_argmax(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
 int64_t run_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_t max_swaps, int64_t* source,
                    cudaStream_t s);
 void run_grade(mtp_model* m, int64_t N, bool fp64, const double* rows, const float* rows_hi,
