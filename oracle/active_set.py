@@ -66,3 +66,39 @@ def classify(gamma, gamma_save, gamma_break):
     configuration and continue); 2: gamma > gamma_break (stop).  Strict comparisons."""
     gamma = np.asarray(gamma)
     return (gamma > gamma_save).astype(np.int32) + (gamma > gamma_break).astype(np.int32)
+
+
+# ------------------------------------------------------------------------------------
+# spherical cut of a neighborhood (Section II.E, option (ii): treat it as a cluster)
+# ------------------------------------------------------------------------------------
+
+def cut_cluster(batch, center, radius):
+    """Every atom j and periodic image n of center's configuration with |x_j + n H - x_c| <
+    radius (the center itself at the origin, first), as a non-periodic cluster: returns
+    (pos relative to the center [M x 3], type [M], source atom [M]).  Order: the center, then
+    ascending (j, n0, n1, n2)."""
+    off = batch["atom_offset"]
+    k = int(np.searchsorted(off, center, side="right") - 1)
+    a0, a1 = off[k], off[k + 1]
+    H = batch["cell"][k].reshape(3, 3)
+    pbc = batch["pbc"][k]
+    xc = batch["pos"][center]
+    # image range per axis from the face distances of the cell
+    vol = abs(np.linalg.det(H))
+    K = []
+    for a in range(3):
+        h = vol / np.linalg.norm(np.cross(H[(a + 1) % 3], H[(a + 2) % 3]))
+        span = np.abs(batch["pos"][a0:a1] @ np.linalg.inv(H)[:, a]).max() + 1.0
+        K.append(int(np.ceil(radius / h + span)) + 1 if pbc[a] else 0)
+    out = [(center, (0, 0, 0))]
+    for j in range(a0, a1):
+        for n0 in range(-K[0], K[0] + 1):
+            for n1 in range(-K[1], K[1] + 1):
+                for n2 in range(-K[2], K[2] + 1):
+                    if j == center and n0 == n1 == n2 == 0:
+                        continue
+                    r = batch["pos"][j] + np.array([n0, n1, n2]) @ H - xc
+                    if np.sqrt(r @ r) < radius:
+                        out.append((j, (n0, n1, n2)))
+    pos = np.array([batch["pos"][j] + np.array(n) @ H - xc for j, n in out])
+    return pos, batch["type"][[j for j, _ in out]].astype(np.int32), np.array([j for j, _ in out], np.int64)

@@ -116,3 +116,37 @@ def test_neighborhood_config_grade_and_classes():
     assert list(AS.neighborhood_config_grade(gam, off)) == [3.0, 0.0, 11.0, 10.0]
     cls = AS.classify(np.array([0.5, 2.0, 2.0000001, 10.0, 10.5]), 2.0, 10.0)
     assert list(cls) == [0, 0, 1, 1, 2]
+
+
+# ---------------------------------------------------------------------------------
+# spherical cut
+# ---------------------------------------------------------------------------------
+
+def test_cut_cluster_matches_the_neighbor_list_at_that_radius():
+    """The cut at radius R is the center plus its neighbor list at cut-off R (the oracle's
+    independent neighbor routine), with the same relative vectors."""
+    from oracle import oracle as O
+    b = synth.fcc_ternary(seed=61, n=3)      # 10.8 A cell: an 8 A sphere needs images
+    for c in (0, 17, 100):
+        pos, ty, src = AS.cut_cluster(b, c, 8.0)
+        off, _, _, r = O.neighbors(b["pos"], b["cell"][0], b["pbc"][0], 8.0)
+        lo, hi = off[c], off[c + 1]
+        assert len(src) == 1 + hi - lo
+        assert src[0] == c and np.allclose(pos[0], 0)
+        got = sorted(map(tuple, np.round(pos[1:], 9)))
+        ref = sorted(map(tuple, np.round(r[lo:hi], 9)))
+        assert got == ref
+        assert (ty == b["type"][src]).all()
+        assert np.sqrt((pos ** 2).sum(1)).max() < 8.0
+
+
+def test_cut_cluster_open_axis():
+    """A non-periodic axis takes no images along it."""
+    b = synth.fcc_ternary(seed=62, n=3)
+    b["pbc"] = np.array([[1, 1, 0]], np.uint8)
+    pos, _, src = AS.cut_cluster(b, 40, 8.0)
+    full, _, _ = AS.cut_cluster(synth.fcc_ternary(seed=62, n=3), 40, 8.0)
+    assert len(src) < len(full)
+    H = b["cell"][0]
+    z_img = np.round((pos[:, 2] + b["pos"][40, 2] - b["pos"][src, 2]) / H[2, 2])
+    assert (z_img == 0).all()
