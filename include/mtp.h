@@ -266,6 +266,19 @@ mtp_status mtp_extract_neighborhoods(const mtp_nbr* nbr, const mtp_batch* batch,
                                      int32_t* type, int32_t* j, int64_t capacity,
                                      int64_t* total, void* stream);
 
+/* Spherical cut (Section II.E step 3, option (ii): an extrapolative neighborhood is cut out
+ * and treated as a non-periodic cluster; the paper's cut radius is 8 A).  For each of the n
+ * DEVICE center atoms, every atom j of its configuration and periodic image n (periodic axes
+ * only) with |x_j + n H - x_c| < radius: CSR off[n+1] (int64, DEVICE), then per cluster atom
+ * its position relative to the center pos[3] (FP64, A; the center itself first, at the
+ * origin, then ascending (j, n0, n1, n2)), species type[] and source atom src[] (int64).
+ * pos/type/src may all be NULL to query the size; *total (HOST) receives the number of
+ * cluster atoms; MTP_ERR_CAPACITY if an output is given and capacity < total.  Needs no
+ * model or neighbor list.  Synchronises `stream`. */
+mtp_status mtp_cut_clusters(const mtp_batch* batch, const int64_t* centers, int64_t n, double radius,
+                            int64_t* off, double* pos, int32_t* type, int64_t* src,
+                            int64_t capacity, int64_t* total, void* stream);
+
 /* Loss of eq. 7 and its gradient with respect to theta:
  *   L = sum_k [ w_e (E_k - E*_k)^2 + w_f sum_i |F_ik - F*_ik|^2 + w_s sum_ab (W_k,ab - W*_k,ab)^2 ].
  * DEVICE inputs E_ref[n_cfg], F_ref[N x 3], W_ref[n_cfg x 9] (NULL allowed if w_s == 0);

@@ -66,6 +66,7 @@ _SIGS = {
     "mtp_set_active_set": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mtp_get_active_inverse": (ctypes.c_int, [_P, _P, _P]),
     "mtp_get_active_set": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_cut_clusters": (ctypes.c_int, [_P, _P, _I64, _D, _P, _P, _P, _P, _I64, _P, _P]),
     "mtp_config_rows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
     "mtp_config_grade": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _D, _D, _P, _P, _P, _P]),
     "mtp_maxvol": (ctypes.c_int, [_P, _P, _I64, _D, _I64, _P, _P, _P]),
@@ -423,6 +424,24 @@ def mtp_extract_neighborhoods(nbr, batch, idx: torch.Tensor, capacity=None, stre
                                            _ptr(ty), _ptr(j), capacity, ctypes.byref(total), _stream(stream)))
     t = total.value
     return {"off": off, "r": r[:t], "type": ty[:t], "j": j[:t]}
+
+
+def mtp_cut_clusters(batch, centers: torch.Tensor, radius=8.0, stream=None):
+    """Non-periodic clusters of radius `radius` around the center atoms: CSR offsets and, per
+    cluster atom, position relative to its center, species and source atom."""
+    centers = centers.to(device="cuda", dtype=torch.int64).contiguous()
+    n = int(centers.numel())
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    total = ctypes.c_int64()
+    _check(lib().mtp_cut_clusters(ctypes.byref(batch.c), _ptr(centers) if n else None, n, float(radius), _ptr(off),
+                                  None, None, None, 0, ctypes.byref(total), _stream(stream)))
+    t = total.value
+    pos = torch.empty((max(t, 1), 3), dtype=torch.float64, device="cuda")
+    ty = torch.empty(max(t, 1), dtype=torch.int32, device="cuda")
+    src = torch.empty(max(t, 1), dtype=torch.int64, device="cuda")
+    _check(lib().mtp_cut_clusters(ctypes.byref(batch.c), _ptr(centers) if n else None, n, float(radius), _ptr(off),
+                                  _ptr(pos), _ptr(ty), _ptr(src), t, ctypes.byref(total), _stream(stream)))
+    return {"off": off, "pos": pos[:t], "type": ty[:t], "src": src[:t]}
 
 
 def mtp_train_step(model, batch, nbr, E_ref, F_ref, W_ref=None, w_e=1.0, w_f=0.01, w_s=0.0, prec="fp64",

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <stdexcept>
@@ -771,6 +772,22 @@ mtp_status mtp_extract_neighborhoods(const mtp_nbr* nb, const mtp_batch* b, cons
     tmp.release();
     *total = t;
     if (t > capacity) throw Fail{MTP_ERR_CAPACITY, "extraction needs " + std::to_string(t) + " neighbor slots"};
+  });
+}
+
+mtp_status mtp_cut_clusters(const mtp_batch* b, const int64_t* centers, int64_t n, double radius, int64_t* off,
+                            double* pos, int32_t* type, int64_t* src, int64_t capacity, int64_t* total,
+                            void* stream) {
+  return guarded([&] {
+    if (!b || !off || !total || (n > 0 && !centers)) throw Fail{MTP_ERR_ARG, "null argument"};
+    if (n < 0 || capacity < 0) throw Fail{MTP_ERR_ARG, "negative count"};
+    if (!(radius > 0.0) || !std::isfinite(radius)) throw Fail{MTP_ERR_ARG, "radius must be positive"};
+    if (b->n_cfg <= 0 || !b->atom_offset || !b->pos || !b->type || !b->cell || !b->pbc)
+      throw Fail{MTP_ERR_ARG, "incomplete batch"};
+    const int64_t t = run_cut_clusters(b, centers, n, radius, off, pos, type, src, capacity, as_stream(stream));
+    *total = t;
+    if ((pos || type || src) && t > capacity)
+      throw Fail{MTP_ERR_CAPACITY, "the clusters need " + std::to_string(t) + " atom slots"};
   });
 }
 
