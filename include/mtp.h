@@ -266,6 +266,31 @@ mtp_status mtp_extract_neighborhoods(const mtp_nbr* nbr, const mtp_batch* batch,
                                      int32_t* type, int32_t* j, int64_t capacity,
                                      int64_t* total, void* stream);
 
+/* BFGS fit of theta (Section II.B: minimise the loss of eq. 7 with BFGS), starting from the
+ * model's parameters; loss and gradient from mtp_train_step (arguments as there).  Variables
+ * u = theta / D, D_p = max(|theta0_p|, 1e-12 max|theta0|); textbook BFGS inverse-Hessian update
+ * (skipped when s.y <= 0; H = (s.y / y.y) I before the first update); backtracking Armijo line
+ * search (step 1, halved up to 40 times, c1 = 1e-4).  Stops when max|dL/du| <= gtol max(1,|L|),
+ * after max_iter accepted steps, or when no step is accepted.  The model is left at the
+ * accepted parameters (read them with mtp_get_params).  HOST outputs (or NULL): the final
+ * loss and the number of accepted steps.  Host driver; each evaluation runs on `stream` and
+ * synchronises it. */
+mtp_status mtp_fit_bfgs(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                        mtp_precision prec, const double* E_ref, const double* F_ref,
+                        const double* W_ref, double w_e, double w_f, double w_s, int64_t max_iter,
+                        double gtol, double* loss, int64_t* iters, void* stream);
+
+/* Current parameter vector theta (HOST out, m FP64). */
+mtp_status mtp_get_params(const mtp_model* model, double* theta, int64_t m);
+
+/* Fitting errors of the current parameters (the check_errors report), HOST report[9]:
+ * energy per atom |E_k - E*_k| / N_k: max, mean, RMS over configurations; force |F_i - F*_i|:
+ * max, mean, RMS over atoms; virial |W_ab - W*_ab| (eV): max, mean, RMS over configurations
+ * and components (zeros if W_ref is NULL).  DEVICE references as in mtp_train_step. */
+mtp_status mtp_fit_errors(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                          mtp_precision prec, const double* E_ref, const double* F_ref,
+                          const double* W_ref, double* report, void* stream);
+
 /* Spherical cut (Section II.E step 3, option (ii): an extrapolative neighborhood is cut out
  * and treated as a non-periodic cluster; the paper's cut radius is 8 A).  For each of the n
  * DEVICE center atoms, every atom j of its configuration and periodic image n (periodic axes

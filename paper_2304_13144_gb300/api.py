@@ -66,6 +66,9 @@ _SIGS = {
     "mtp_set_active_set": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mtp_get_active_inverse": (ctypes.c_int, [_P, _P, _P]),
     "mtp_get_active_set": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_fit_bfgs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _I64, _D, _P, _P, _P]),
+    "mtp_fit_errors": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "mtp_get_params": (ctypes.c_int, [_P, _P, _I64]),
     "mtp_cut_clusters": (ctypes.c_int, [_P, _P, _I64, _D, _P, _P, _P, _P, _I64, _P, _P]),
     "mtp_config_rows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
     "mtp_config_grade": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _D, _D, _P, _P, _P, _P]),
@@ -456,6 +459,40 @@ def mtp_train_step(model, batch, nbr, E_ref, F_ref, W_ref=None, w_e=1.0, w_f=0.0
                                 _ptr(W_ref), float(w_e), float(w_f), float(w_s), _ptr(loss), _ptr(grad),
                                 _stream(stream)))
     return loss, grad
+
+
+def mtp_get_params(model):
+    out = np.zeros(model.n_params)
+    _check(lib().mtp_get_params(model.h, _ptr(out), out.size))
+    return out
+
+
+def _refs(E_ref, F_ref, W_ref):
+    E_ref = torch.as_tensor(E_ref).to(device="cuda", dtype=torch.float64).contiguous()
+    F_ref = torch.as_tensor(F_ref).to(device="cuda", dtype=torch.float64).contiguous()
+    if W_ref is not None:
+        W_ref = torch.as_tensor(W_ref).to(device="cuda", dtype=torch.float64).contiguous()
+    return E_ref, F_ref, W_ref
+
+
+def mtp_fit_bfgs(model, batch, nbr, E_ref, F_ref, W_ref=None, w_e=1.0, w_f=0.01, w_s=0.0, prec="fp64",
+                 max_iter=100, gtol=1e-8, stream=None):
+    """BFGS fit of the model's parameters; returns (final loss, accepted steps)."""
+    E_ref, F_ref, W_ref = _refs(E_ref, F_ref, W_ref)
+    loss, iters = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().mtp_fit_bfgs(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(E_ref), _ptr(F_ref),
+                              _ptr(W_ref), float(w_e), float(w_f), float(w_s), int(max_iter), float(gtol),
+                              ctypes.byref(loss), ctypes.byref(iters), _stream(stream)))
+    return loss.value, iters.value
+
+
+def mtp_fit_errors(model, batch, nbr, E_ref, F_ref, W_ref=None, prec="fp64", stream=None):
+    """[E/atom max, mean, RMS, |dF| max, mean, RMS, |dW| max, mean, RMS]."""
+    E_ref, F_ref, W_ref = _refs(E_ref, F_ref, W_ref)
+    rep = np.zeros(9)
+    _check(lib().mtp_fit_errors(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(E_ref), _ptr(F_ref),
+                                _ptr(W_ref), _ptr(rep), _stream(stream)))
+    return rep
 
 
 def mtp_profiler_enable(on=True):

@@ -540,6 +540,14 @@ mtp_status mtp_set_params(mtp_model* md, const double* theta, int64_t m) {
   });
 }
 
+mtp_status mtp_get_params(const mtp_model* md, double* theta, int64_t m) {
+  return guarded([&] {
+    check_model(md);
+    if (!theta || m != md->sched.n_params) throw Fail{MTP_ERR_ARG, "theta size mismatch"};
+    std::copy(md->theta.begin(), md->theta.end(), theta);
+  });
+}
+
 mtp_status mtp_set_active_set(mtp_model* md, const double* A, int64_t m, void* stream) {
   return guarded([&] {
     check_model(md);
