@@ -280,6 +280,16 @@ mtp_status mtp_fit_bfgs(mtp_model* model, const mtp_batch* batch, const mtp_nbr*
                         const double* W_ref, double w_e, double w_f, double w_s, int64_t max_iter,
                         double gtol, double* loss, int64_t* iters, void* stream);
 
+/* Autotuner for the per-neighborhood kernel's launch shape (the paper has no counterpart):
+ * times the pass that mtp_step makes (energies, forces, virial, and the grade when an active
+ * set is loaded) on this batch at every feasible number of warps per block (1..8 for the
+ * specialised mixed kernel, 1, 2, 4 for the generic kernel; blocks per SM then follow from
+ * the occupancy), keeps the fastest in the model for later calls of this precision's kernel,
+ * and returns it (HOST warps, HOST ms = its best time of three) -- either may be NULL.
+ * Synchronises `stream`. */
+mtp_status mtp_autotune(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                        mtp_precision prec, int32_t* warps, double* ms, void* stream);
+
 /* Current parameter vector theta (HOST out, m FP64). */
 mtp_status mtp_get_params(const mtp_model* model, double* theta, int64_t m);
 

@@ -66,6 +66,7 @@ _SIGS = {
     "mtp_set_active_set": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mtp_get_active_inverse": (ctypes.c_int, [_P, _P, _P]),
     "mtp_get_active_set": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "mtp_fit_bfgs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _I64, _D, _P, _P, _P]),
     "mtp_fit_errors": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "mtp_get_params": (ctypes.c_int, [_P, _P, _I64]),
@@ -459,6 +460,14 @@ def mtp_train_step(model, batch, nbr, E_ref, F_ref, W_ref=None, w_e=1.0, w_f=0.0
                                 _ptr(W_ref), float(w_e), float(w_f), float(w_s), _ptr(loss), _ptr(grad),
                                 _stream(stream)))
     return loss, grad
+
+
+def mtp_autotune(model, batch, nbr, prec="mixed", stream=None):
+    """Pick the per-neighborhood kernel's warps per block by timing; returns (warps, ms)."""
+    w, ms = ctypes.c_int32(), ctypes.c_double()
+    _check(lib().mtp_autotune(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), ctypes.byref(w), ctypes.byref(ms),
+                              _stream(stream)))
+    return w.value, ms.value
 
 
 def mtp_get_params(model):

@@ -540,6 +540,57 @@ mtp_status mtp_set_params(mtp_model* md, const double* theta, int64_t m) {
   });
 }
 
+mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec, int32_t* warps,
+                        double* ms, void* stream) {
+  return guarded([&] {
+    check_run(md, b, nb);
+    if (prec != MTP_FP64 && prec != MTP_MIXED) throw Fail{MTP_ERR_ARG, "unknown precision"};
+    cudaStream_t s = as_stream(stream);
+    const int64_t N = nb->n_atoms, K = nb->n_cfg;
+    DevBuf out;
+    out.ensure((K * 10 + 4 * std::max<int64_t>(N, 1)) * sizeof(double) + 64, s);
+    double* E = out.as<double>();
+    double* W = E + K;
+    double* F = W + 9 * K;
+    double* gam = F + 3 * std::max<int64_t>(N, 1);
+    double* gamma = md->have_ainv ? gam : nullptr;
+    // the pass that mtp_step makes (energies, forces, virial and, with an active set, the grade)
+    auto run = [&] { efs_and_grade(md, b, nb, prec, E, nullptr, F, W, 0.0, gamma, nullptr, nullptr, nullptr, s); };
+    run();
+    const bool fast = md->last_fast;
+    int& knob = fast ? md->tune_warps_fast : md->tune_warps_generic;
+    const int max_w = fast ? 8 : 4;
+    cudaEvent_t e0, e1;
+    MTP_CUDA(cudaEventCreate(&e0));
+    MTP_CUDA(cudaEventCreate(&e1));
+    int best_w = 0, last_used = -1;
+    float best_ms = 0.f;
+    for (int w = max_w; w >= 1; --w) {
+      knob = w;
+      run();   // warm-up at this shape
+      if (md->last_warps == last_used) continue;   // clamped to a shape already timed
+      last_used = md->last_warps;
+      float t_min = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        MTP_CUDA(cudaEventRecord(e0, s));
+        run();
+        MTP_CUDA(cudaEventRecord(e1, s));
+        MTP_CUDA(cudaEventSynchronize(e1));
+        float t = 0.f;
+        MTP_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        if (rep == 0 || t < t_min) t_min = t;
+      }
+      if (best_w == 0 || t_min < best_ms) { best_ms = t_min; best_w = md->last_warps; }
+    }
+    MTP_CUDA(cudaEventDestroy(e0));
+    MTP_CUDA(cudaEventDestroy(e1));
+    knob = best_w;
+    MTP_CUDA(cudaStreamSynchronize(s));
+    if (warps) *warps = best_w;
+    if (ms) *ms = best_ms;
+  });
+}
+
 mtp_status mtp_get_params(const mtp_model* md, double* theta, int64_t m) {
   return guarded([&] {
     check_model(md);

@@ -165,6 +165,12 @@ struct mtp_model {
   mtp::DevBuf ws_red;          // reductions
   mtp::DevBuf err_flag;        // unsigned
   bool force_generic = false;  // route the mixed path through the generic kernel (cross-checks)
+  // launch shape of the per-neighborhood kernels: warps per block (0 = largest that fits),
+  // chosen by mtp_autotune; last_warps records the shape of the latest launch
+  int tune_warps_fast = 0;
+  int tune_warps_generic = 0;
+  int last_warps = 0;
+  bool last_fast = false;
 };
 
 struct mtp_nbr {

@@ -110,6 +110,7 @@ struct SiteParams {
   int64_t n_work;
   SiteOutputs o;
   Layout L;
+  int warps_hint;   // warps per block requested (0: the largest that fits)
 };
 
 // Load r_ij (and its tangent) for pair p of center i.
@@ -446,11 +447,12 @@ __global__ void __launch_bounds__(kWarps * 32) site_kernel(SiteParams P) {
   }
 }
 
+// Launches the kernel; returns the warps per block used.
 template <class S, class R, int MODE>
-void launch_sites(const SiteParams& P0, int* grid_used, cudaStream_t s) {
+int launch_sites(const SiteParams& P0, int* grid_used, cudaStream_t s) {
   SiteParams P = P0;
   // as many warps per block (up to kWarps) as the per-warp value arrays leave room for
-  int warps = kWarps;
+  int warps = (P.warps_hint > 0) ? std::min(P.warps_hint, kWarps) : kWarps;
   P.L = make_layout<S, R>(P.d, warps);
   while (warps > 1 && P.L.total > 227 * 1024) {
     warps >>= 1;
@@ -473,11 +475,12 @@ void launch_sites(const SiteParams& P0, int* grid_used, cudaStream_t s) {
     if (*grid_used > 0) grid = std::min(grid, *grid_used);
     *grid_used = grid;
   }
-  if (P.n_work == 0) return;
+  if (P.n_work == 0) return warps;
   const char* name = (MODE & M_TAN) ? "site_tangent" : (MODE & M_EFS) ? ((MODE & M_ROWS) ? "site_efs_rows" : "site_efs") : "site_rows";
   ProfRegion pr(name, s);
   kern<<<grid, warps * 32, P.L.total, s>>>(P);
   MTP_CUDA(cudaGetLastError());
+  return warps;
 }
 
 }  // namespace
@@ -496,6 +499,8 @@ void run_sites(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, bool fp64, c
                bool tangent, int* grid_used, cudaStream_t s) {
   if (!fp64 && !tangent && !m->force_generic && run_sites_fast(m, b, nb, o, s)) return;
   SiteParams P{};
+  P.warps_hint = m->tune_warps_generic;
+  m->last_fast = false;
   P.d = m->ds;
   P.nb = nb->dn;
   P.pos = b->pos;
@@ -506,19 +511,19 @@ void run_sites(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, bool fp64, c
   const bool efs = o.V != nullptr;
   const bool rows = o.rows != nullptr || o.rows_hi != nullptr;
   if (tangent) {
-    if (fp64) launch_sites<Dual<double>, double, M_TAN>(P, grid_used, s);
-    else launch_sites<Dual<float>, float, M_TAN>(P, grid_used, s);
+    if (fp64) m->last_warps = launch_sites<Dual<double>, double, M_TAN>(P, grid_used, s);
+    else m->last_warps = launch_sites<Dual<float>, float, M_TAN>(P, grid_used, s);
     return;
   }
   if (efs && rows) {
-    if (fp64) launch_sites<double, double, M_EFS | M_ROWS>(P, grid_used, s);
-    else launch_sites<float, float, M_EFS | M_ROWS>(P, grid_used, s);
+    if (fp64) m->last_warps = launch_sites<double, double, M_EFS | M_ROWS>(P, grid_used, s);
+    else m->last_warps = launch_sites<float, float, M_EFS | M_ROWS>(P, grid_used, s);
   } else if (efs) {
-    if (fp64) launch_sites<double, double, M_EFS>(P, grid_used, s);
-    else launch_sites<float, float, M_EFS>(P, grid_used, s);
+    if (fp64) m->last_warps = launch_sites<double, double, M_EFS>(P, grid_used, s);
+    else m->last_warps = launch_sites<float, float, M_EFS>(P, grid_used, s);
   } else if (rows) {
-    if (fp64) launch_sites<double, double, M_ROWS>(P, grid_used, s);
-    else launch_sites<float, float, M_ROWS>(P, grid_used, s);
+    if (fp64) m->last_warps = launch_sites<double, double, M_ROWS>(P, grid_used, s);
+    else m->last_warps = launch_sites<float, float, M_ROWS>(P, grid_used, s);
   } else {
     throw Fail{MTP_ERR_ARG, "no output requested"};
   }

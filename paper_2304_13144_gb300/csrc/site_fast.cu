@@ -618,7 +618,10 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   const size_t fixed = P.c_bytes + P.tab_bytes + P.sched_bytes;
   const size_t limit = 227 * 1024;
   if (fixed + 2 * P.warp_bytes > limit) return false;
-  const int nwarps = static_cast<int>(std::min<size_t>(kMaxWarpsF, (limit - fixed) / P.warp_bytes));
+  int nwarps = static_cast<int>(std::min<size_t>(kMaxWarpsF, (limit - fixed) / P.warp_bytes));
+  if (m->tune_warps_fast > 0) nwarps = std::min(nwarps, m->tune_warps_fast);
+  m->last_warps = nwarps;
+  m->last_fast = true;
   P.total = fixed + nwarps * P.warp_bytes;
   const int nu0 = d.nu_max, nr = d.n_rad;
   if (nr == 2 && nu0 == 2) { dispatch_mode<2, 2>(P, nwarps, efs, rows, s); return true; }
