@@ -284,7 +284,9 @@ mtp_status mtp_fit_bfgs(mtp_model* model, const mtp_batch* batch, const mtp_nbr*
  * times the pass that mtp_step makes (energies, forces, virial, and the grade when an active
  * set is loaded) on this batch at every feasible number of warps per block (1..8 for the
  * specialised mixed kernel, 1, 2, 4 for the generic kernel; blocks per SM then follow from
- * the occupancy), keeps the fastest in the model for later calls of this precision's kernel,
+ * the occupancy) and, for the level-20 shape of the mixed kernel, with the forward part of the
+ * contraction schedule in shared or in global memory; keeps the fastest in the model for later
+ * calls of this precision's kernel,
  * and returns it (HOST warps, HOST ms = its best time of three) -- either may be NULL.
  * Synchronises `stream`. */
 mtp_status mtp_autotune(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,

@@ -556,6 +556,8 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     double* gamma = md->have_ainv ? gam : nullptr;
     // the pass that mtp_step makes (energies, forces, virial and, with an active set, the grade)
     auto run = [&] { efs_and_grade(md, b, nb, prec, E, nullptr, F, W, 0.0, gamma, nullptr, nullptr, nullptr, s); };
+    md->tune_warps_fast = md->tune_warps_generic = 0;
+    md->tune_fwd_global = -1;
     run();
     const bool fast = md->last_fast;
     int& knob = fast ? md->tune_warps_fast : md->tune_warps_generic;
@@ -563,28 +565,35 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     cudaEvent_t e0, e1;
     MTP_CUDA(cudaEventCreate(&e0));
     MTP_CUDA(cudaEventCreate(&e1));
-    int best_w = 0, last_used = -1;
+    int best_w = 0, best_p = -1;
     float best_ms = 0.f;
-    for (int w = max_w; w >= 1; --w) {
-      knob = w;
-      run();   // warm-up at this shape
-      if (md->last_warps == last_used) continue;   // clamped to a shape already timed
-      last_used = md->last_warps;
-      float t_min = 0.f;
-      for (int rep = 0; rep < 3; ++rep) {
-        MTP_CUDA(cudaEventRecord(e0, s));
-        run();
-        MTP_CUDA(cudaEventRecord(e1, s));
-        MTP_CUDA(cudaEventSynchronize(e1));
-        float t = 0.f;
-        MTP_CUDA(cudaEventElapsedTime(&t, e0, e1));
-        if (rep == 0 || t < t_min) t_min = t;
+    // candidate shapes: (forward-slab placement, warps per block); the generic kernel has only warps
+    for (int place = 0; place < (fast ? 2 : 1); ++place) {
+      if (fast) md->tune_fwd_global = place;
+      int last_used = -1;
+      for (int w = max_w; w >= 1; --w) {
+        knob = w;
+        run();   // warm-up at this shape
+        if (fast && static_cast<int>(md->last_fwd_global) != place) break;   // placement unavailable
+        if (md->last_warps == last_used) continue;   // clamped to a shape already timed
+        last_used = md->last_warps;
+        float t_min = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+          MTP_CUDA(cudaEventRecord(e0, s));
+          run();
+          MTP_CUDA(cudaEventRecord(e1, s));
+          MTP_CUDA(cudaEventSynchronize(e1));
+          float t = 0.f;
+          MTP_CUDA(cudaEventElapsedTime(&t, e0, e1));
+          if (rep == 0 || t < t_min) t_min = t;
+        }
+        if (best_w == 0 || t_min < best_ms) { best_ms = t_min; best_w = md->last_warps; best_p = place; }
       }
-      if (best_w == 0 || t_min < best_ms) { best_ms = t_min; best_w = md->last_warps; }
     }
     MTP_CUDA(cudaEventDestroy(e0));
     MTP_CUDA(cudaEventDestroy(e1));
     knob = best_w;
+    if (fast) md->tune_fwd_global = best_p;
     MTP_CUDA(cudaStreamSynchronize(s));
     if (warps) *warps = best_w;
     if (ms) *ms = best_ms;

@@ -168,6 +168,8 @@ struct mtp_model {
   // launch shape of the per-neighborhood kernels: warps per block (0 = largest that fits),
   // chosen by mtp_autotune; last_warps records the shape of the latest launch
   int tune_warps_fast = 0;
+  int tune_fwd_global = -1;    // forward schedule in global memory: -1 automatic, 0 no, 1 yes
+  bool last_fwd_global = false;
   int tune_warps_generic = 0;
   int last_warps = 0;
   bool last_fast = false;

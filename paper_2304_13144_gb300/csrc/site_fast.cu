@@ -248,7 +248,9 @@ constexpr int kMaxWarpsF = 8;
 constexpr int kNQ = 8;   // radial polynomials of the specialised kernel (other N_Q: generic kernel)
 enum : int { F_EFS = 1, F_ROWS = 2 };
 
-template <int NR, int NU0, int MODE>
+// FG: the forward slab stays in global memory (read through L1) instead of shared memory, which
+// leaves room for one more warp per SM on the level-20 shape.
+template <int NR, int NU0, int MODE, bool FG>
 __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParams P) {
   using Sh = Shape<NR, NU0>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -279,14 +281,14 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
   }
   // the contraction schedule, staged once per (persistent) block: every warp reads it per atom
   uint32_t* sched = reinterpret_cast<uint32_t*>(smem + P.c_bytes + P.tab_bytes);
-  copy_words(sched + P.o_fslab, d.fslab, d.fslab_words);
+  if (!FG) copy_words(sched + P.o_fslab, d.fslab, d.fslab_words);
   copy_words(sched + P.o_fround, reinterpret_cast<const uint32_t*>(d.fround), 4 * d.n_fround);
   copy_words(sched + P.o_frdst, reinterpret_cast<const uint32_t*>(d.fr_dst), 32 * d.n_fround);
   copy_words(sched + P.o_rslab, d.rslab, d.rslab_words);
   copy_words(sched + P.o_rround, reinterpret_cast<const uint32_t*>(d.rround), 4 * d.n_rround);
   copy_words(sched + P.o_rrval, reinterpret_cast<const uint32_t*>(d.rr_val), 32 * d.n_rround);
   copy_words(sched + P.o_seed, reinterpret_cast<const uint32_t*>(d.seed_f), d.n_vals);
-  const uint32_t* s_fslab = sched + P.o_fslab;
+  const uint32_t* s_fslab = FG ? d.fslab : sched + P.o_fslab;
   const int4* s_fround = reinterpret_cast<const int4*>(sched + P.o_fround);
   const int* s_frdst = reinterpret_cast<const int*>(sched + P.o_frdst);
   const uint32_t* s_rslab = sched + P.o_rslab;
@@ -498,7 +500,8 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
       float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
       int it = 0;
       for (; it + 2 <= rd.x; it += 2) {
-        const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32];
+        const uint32_t w0 = FG ? __ldg(slab + 32 * it) : slab[32 * it];
+        const uint32_t w1 = FG ? __ldg(slab + 32 * it + 32) : slab[32 * it + 32];
         const float c0 = coef[w0 >> 24], c1 = coef[w1 >> 24];
         const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u, x1 = w1 & 4095u, y1 = (w1 >> 12) & 4095u;
         a0 = fmaf(c0, v0[x0] * v0[y0], a0);
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         b1 = fmaf(c1, v1[x1] * v1[y1], b1);
       }
       if (it < rd.x) {
-        const uint32_t w0 = slab[32 * it];
+        const uint32_t w0 = FG ? __ldg(slab + 32 * it) : slab[32 * it];
         const float c0 = coef[w0 >> 24];
         const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u;
         a0 = fmaf(c0, v0[x0] * v0[y0], a0);
@@ -555,9 +558,9 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
   }
 }
 
-template <int NR, int NU0, int MODE>
+template <int NR, int NU0, int MODE, bool FG>
 void launch_fast(FastParams P, int nwarps, cudaStream_t s) {
-  auto kern = site_fast_kernel<NR, NU0, MODE>;
+  auto kern = site_fast_kernel<NR, NU0, MODE, FG>;
   MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(P.total)));
   int dev = 0, nsm = 0, per_sm = 0;
   MTP_CUDA(cudaGetDevice(&dev));
@@ -572,11 +575,11 @@ void launch_fast(FastParams P, int nwarps, cudaStream_t s) {
   MTP_CUDA(cudaGetLastError());
 }
 
-template <int NR, int NU0>
+template <int NR, int NU0, bool FG>
 void dispatch_mode(FastParams P, int nwarps, bool efs, bool rows, cudaStream_t s) {
-  if (efs && rows) launch_fast<NR, NU0, F_EFS | F_ROWS>(P, nwarps, s);
-  else if (efs) launch_fast<NR, NU0, F_EFS>(P, nwarps, s);
-  else launch_fast<NR, NU0, F_ROWS>(P, nwarps, s);
+  if (efs && rows) launch_fast<NR, NU0, F_EFS | F_ROWS, FG>(P, nwarps, s);
+  else if (efs) launch_fast<NR, NU0, F_EFS, FG>(P, nwarps, s);
+  else launch_fast<NR, NU0, F_ROWS, FG>(P, nwarps, s);
 }
 
 }  // namespace
@@ -604,30 +607,44 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   P.tab_bytes = ((256 + d.n_mom) * sizeof(float) + 15) & ~size_t(15);
   P.warp_bytes = ((4 * static_cast<size_t>(P.NV) + 32 * (d.n_rad + d.n_q) + 2 * P.CBN) * sizeof(float) +
                   32 * sizeof(int) + 15) & ~size_t(15);
-  // shared-memory copy of the schedule (32-bit words)
-  int w = 0;
-  auto take = [&](int n) { const int o = w; w += (n + 3) & ~3; return o; };
-  P.o_fslab = take(d.fslab_words);
-  P.o_fround = take(4 * d.n_fround);
-  P.o_frdst = take(32 * d.n_fround);
-  P.o_rslab = take(d.rslab_words);
-  P.o_rround = take(4 * d.n_rround);
-  P.o_rrval = take(32 * d.n_rround);
-  P.o_seed = take(d.n_vals);
-  P.sched_bytes = static_cast<size_t>(w) * 4;
-  const size_t fixed = P.c_bytes + P.tab_bytes + P.sched_bytes;
+  // shared-memory copy of the schedule (32-bit words); fwd_global: without the forward slab
+  const int nu0 = d.nu_max, nr = d.n_rad;
+  const bool fg_shape = nr == 5 && nu0 == 8;   // the shape with a global-forward instantiation
   const size_t limit = 227 * 1024;
-  if (fixed + 2 * P.warp_bytes > limit) return false;
-  int nwarps = static_cast<int>(std::min<size_t>(kMaxWarpsF, (limit - fixed) / P.warp_bytes));
+  auto layout = [&](bool fg, FastParams& Q) {
+    int w = 0;
+    auto take = [&](int n) { const int o = w; w += (n + 3) & ~3; return o; };
+    Q.o_fslab = fg ? 0 : take(d.fslab_words);
+    Q.o_fround = take(4 * d.n_fround);
+    Q.o_frdst = take(32 * d.n_fround);
+    Q.o_rslab = take(d.rslab_words);
+    Q.o_rround = take(4 * d.n_rround);
+    Q.o_rrval = take(32 * d.n_rround);
+    Q.o_seed = take(d.n_vals);
+    Q.sched_bytes = static_cast<size_t>(w) * 4;
+    const size_t fixed = Q.c_bytes + Q.tab_bytes + Q.sched_bytes;
+    if (fixed + 2 * Q.warp_bytes > limit) return 0;
+    return static_cast<int>(std::min<size_t>(kMaxWarpsF, (limit - fixed) / Q.warp_bytes));
+  };
+  FastParams Ps = P, Pg = P;
+  const int ws = layout(false, Ps);
+  const int wg = fg_shape ? layout(true, Pg) : 0;
+  // placement: the tuned one, else the one with more warps per SM (shared memory on ties)
+  bool fg = m->tune_fwd_global >= 0 ? (m->tune_fwd_global == 1 && wg > 0) : (wg > ws);
+  if (!fg && ws == 0) fg = wg > 0;
+  if (!fg && ws == 0) return false;
+  P = fg ? Pg : Ps;
+  int nwarps = fg ? wg : ws;
   if (m->tune_warps_fast > 0) nwarps = std::min(nwarps, m->tune_warps_fast);
   m->last_warps = nwarps;
   m->last_fast = true;
-  P.total = fixed + nwarps * P.warp_bytes;
-  const int nu0 = d.nu_max, nr = d.n_rad;
-  if (nr == 2 && nu0 == 2) { dispatch_mode<2, 2>(P, nwarps, efs, rows, s); return true; }
-  if (nr == 3 && nu0 == 4) { dispatch_mode<3, 4>(P, nwarps, efs, rows, s); return true; }
-  if (nr == 4 && nu0 == 6) { dispatch_mode<4, 6>(P, nwarps, efs, rows, s); return true; }
-  if (nr == 5 && nu0 == 8) { dispatch_mode<5, 8>(P, nwarps, efs, rows, s); return true; }
+  m->last_fwd_global = fg;
+  P.total = P.c_bytes + P.tab_bytes + P.sched_bytes + nwarps * P.warp_bytes;
+  if (fg) { dispatch_mode<5, 8, true>(P, nwarps, efs, rows, s); return true; }
+  if (nr == 2 && nu0 == 2) { dispatch_mode<2, 2, false>(P, nwarps, efs, rows, s); return true; }
+  if (nr == 3 && nu0 == 4) { dispatch_mode<3, 4, false>(P, nwarps, efs, rows, s); return true; }
+  if (nr == 4 && nu0 == 6) { dispatch_mode<4, 6, false>(P, nwarps, efs, rows, s); return true; }
+  if (nr == 5 && nu0 == 8) { dispatch_mode<5, 8, false>(P, nwarps, efs, rows, s); return true; }
   return false;
 }
 
