@@ -9,6 +9,8 @@
 #include <thrust/iterator/counting_iterator.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 
 #include "mtp_internal.h"
@@ -23,16 +25,40 @@ template <class R>
 __global__ void k_forces(DevNbr nb, const R* G, double* F) {
   int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= nb.n_atoms) return;
-  double f0 = 0, f1 = 0, f2 = 0;
-  for (int64_t p = nb.off[i]; p < nb.off[i + 1]; ++p) {
-    const int64_t q = nb.prev[p];
-    f0 += static_cast<double>(G[3 * p + 0]) - static_cast<double>(G[3 * q + 0]);
-    f1 += static_cast<double>(G[3 * p + 1]) - static_cast<double>(G[3 * q + 1]);
-    f2 += static_cast<double>(G[3 * p + 2]) - static_cast<double>(G[3 * q + 2]);
+  if constexpr (std::is_same<R, float>::value) {
+    // FP32 gradients: each component summed as an unevaluated pair hi + lo of floats with
+    // error-free additions (TwoSum), so the sum is as accurate as an FP64 accumulation while
+    // running on the FP32 pipes (FP64 throughput is a small fraction of FP32 on this GPU)
+    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+    auto add = [](float& hi, float& lo, float x) {
+      const float s = __fadd_rn(hi, x);
+      const float bb = __fsub_rn(s, hi);
+      const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+      hi = s;
+      lo = __fadd_rn(lo, err);
+    };
+    for (int64_t p = nb.off[i]; p < nb.off[i + 1]; ++p) {
+      const int64_t q = nb.prev[p];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        add(h[c], l[c], G[3 * p + c]);
+        add(h[c], l[c], -G[3 * q + c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[3 * i + c] = static_cast<double>(h[c]) + static_cast<double>(l[c]);
+  } else {
+    double f0 = 0, f1 = 0, f2 = 0;
+    for (int64_t p = nb.off[i]; p < nb.off[i + 1]; ++p) {
+      const int64_t q = nb.prev[p];
+      f0 += static_cast<double>(G[3 * p + 0]) - static_cast<double>(G[3 * q + 0]);
+      f1 += static_cast<double>(G[3 * p + 1]) - static_cast<double>(G[3 * q + 1]);
+      f2 += static_cast<double>(G[3 * p + 2]) - static_cast<double>(G[3 * q + 2]);
+    }
+    F[3 * i + 0] = f0;
+    F[3 * i + 1] = f1;
+    F[3 * i + 2] = f2;
   }
-  F[3 * i + 0] = f0;
-  F[3 * i + 1] = f1;
-  F[3 * i + 2] = f2;
 }
 
 // one block per segment (cfg, a0, a1): partial[seg][0] = sum V, [1..9] = sum W
