@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
       for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
       if (lane == 0) P.o.V[i] = static_cast<double>(acc) + d.theta_d[zi];
     }
-    float Wl[9];   // this lane's pairs (at most a few terms) in FP32; the warp sum below in FP64
+    float Wl[9];   // this lane's pairs (at most a few terms)
 #pragma unroll
     for (int k = 0; k < 9; ++k) Wl[k] = 0.f;
     for (int base = 0; base < np; base += 32) {
@@ -419,9 +419,11 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
     if (MODE & F_EFS) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        double v = static_cast<double>(Wl[k]);
+        // the neighborhood's virial in FP32 like its forces (FP64 instructions are scarce on this
+        // GPU); the sums over atoms are FP64
+        float v = Wl[k];
         for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-        if (lane == 0) P.o.Wat[9 * i + k] = v;
+        if (lane == 0) P.o.Wat[9 * i + k] = static_cast<double>(v);
       }
     }
     if ((MODE & F_ROWS) && !P.row_stage) {
