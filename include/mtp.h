@@ -292,6 +292,23 @@ mtp_status mtp_fit_bfgs(mtp_model* model, const mtp_batch* batch, const mtp_nbr*
 mtp_status mtp_autotune(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
                         mtp_precision prec, int32_t* warps, double* ms, void* stream);
 
+/* Checkpoint (the paper keeps theta, the active set and its mode in its .almtp file): the
+ * model's descriptor, theta and, if loaded, the active-set matrix A, in a HOST byte buffer
+ * (magic "MTP1", version 1, then mtp_desc, m, theta[m] FP64, a flag and A[m x m] FP64, native
+ * byte order).  buffer == NULL queries the size (*size, HOST); MTP_ERR_CAPACITY if capacity <
+ * size.  mtp_restore makes a new model from such a buffer (A re-factorised on the GPU); the
+ * caller frees it with mtp_free_model. */
+mtp_status mtp_save(const mtp_model* model, void* buffer, int64_t capacity, int64_t* size, void* stream);
+mtp_status mtp_restore(const void* buffer, int64_t size, mtp_model** model, void* stream);
+
+/* Host-side fault injection for tests of the failure paths (no GPU fault is made):
+ * MTP_FAULT_DEVICE_ALLOC makes the next `count` growths of a library workspace fail as a device
+ * allocation failure (MTP_ERR_CUDA); MTP_FAULT_NEIGHBOR_OVERFLOW flags the next `count`
+ * neighbor fills as overflowing their counted capacity (the build repeats a failed fill once,
+ * then returns MTP_ERR_CAPACITY).  count = 0 disarms.  Process-wide. */
+enum { MTP_FAULT_DEVICE_ALLOC = 1, MTP_FAULT_NEIGHBOR_OVERFLOW = 2 };
+mtp_status mtp_debug_inject(int fault, int count);
+
 /* Current parameter vector theta (HOST out, m FP64). */
 mtp_status mtp_get_params(const mtp_model* model, double* theta, int64_t m);
 

@@ -66,6 +66,9 @@ _SIGS = {
     "mtp_set_active_set": (ctypes.c_int, [_P, _P, _I64, _P]),
     "mtp_get_active_inverse": (ctypes.c_int, [_P, _P, _P]),
     "mtp_get_active_set": (ctypes.c_int, [_P, _P, _P]),
+    "mtp_save": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "mtp_restore": (ctypes.c_int, [_P, _I64, _P, _P]),
+    "mtp_debug_inject": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "mtp_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "mtp_fit_bfgs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _I64, _D, _P, _P, _P]),
     "mtp_fit_errors": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
@@ -468,6 +471,36 @@ def mtp_autotune(model, batch, nbr, prec="mixed", stream=None):
     _check(lib().mtp_autotune(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), ctypes.byref(w), ctypes.byref(ms),
                               _stream(stream)))
     return w.value, ms.value
+
+
+def mtp_save(model, stream=None) -> bytes:
+    """Checkpoint of the model (descriptor, theta, active set) as bytes."""
+    size = ctypes.c_int64()
+    _check(lib().mtp_save(model.h, None, 0, ctypes.byref(size), _stream(stream)))
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib().mtp_save(model.h, buf, size.value, ctypes.byref(size), _stream(stream)))
+    return buf.raw[:size.value]
+
+
+def mtp_restore(blob: bytes, stream=None) -> Model:
+    """A new model from a checkpoint made by mtp_save."""
+    m = Model.__new__(Model)
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    _check(lib().mtp_restore(buf, len(blob), ctypes.byref(h), _stream(stream)))
+    m.h = h
+    m.desc = None
+    m.sizes = m.model_sizes()
+    return m
+
+
+MTP_FAULT_DEVICE_ALLOC = 1
+MTP_FAULT_NEIGHBOR_OVERFLOW = 2
+
+
+def mtp_debug_inject(fault, count):
+    """Arm a host-side fault for the next `count` events (0 disarms)."""
+    _check(lib().mtp_debug_inject(int(fault), int(count)))
 
 
 def mtp_get_params(model):

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -16,9 +17,20 @@ namespace mtp {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+std::atomic<int> g_inject_alloc{0};
+std::atomic<int> g_inject_overflow{0};
+
+bool take_injected(std::atomic<int>& c) {
+  int v = c.load();
+  while (v > 0)
+    if (c.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+
 void DevBuf::ensure(size_t need, cudaStream_t s) {
   if (need == 0) need = 16;
   if (bytes >= need) return;
+  if (take_injected(g_inject_alloc)) throw Fail{MTP_ERR_CUDA, "device allocation failed (injected fault)"};
   if (p) MTP_CUDA(cudaFreeAsync(p, s));
   p = nullptr;
   bytes = 0;
@@ -220,6 +232,30 @@ void upload_schedule(mtp_model* md) {
         for (int it = 0; it < L; ++it)
           for (int l = 0; l < 32; ++l) rslab.push_back(it < static_cast<int>(ord[l].size()) ? ord[l][it] : pad);
       }
+  }
+  // every index the kernels will read from the schedule, checked on the host before upload
+  {
+    auto bad = [](const char* what) { throw Fail{MTP_ERR_NUMERIC, std::string("schedule index out of range: ") + what}; };
+    const uint32_t ncf = static_cast<uint32_t>(coef_f.size());
+    const uint32_t unv = static_cast<uint32_t>(nv);
+    for (uint32_t w : fslab)
+      if ((w & 4095u) >= unv || ((w >> 12) & 4095u) >= unv || (w >> 24) >= ncf) bad("forward slab");
+    for (uint32_t w : rslab)
+      if ((w & 4095u) >= unv || ((w >> 12) & 4095u) >= unv || (w >> 24) >= ncf) bad("reverse slab");
+    for (int x : fr_dst)
+      if (x != -1 && (x < nm || x >= nv)) bad("forward destinations");
+    for (int x : rr_val)
+      if (x != -1 && (x < 0 || x >= nv)) bad("reverse values");
+    for (size_t r = 0; r < fround.size(); r += 4)
+      if (fround[r + 1] < 0 || static_cast<size_t>(fround[r + 1]) + 32 * static_cast<size_t>(fround[r]) > fslab.size())
+        bad("forward rounds");
+    for (size_t r = 0; r < rround.size(); r += 4)
+      if (rround[r + 1] < 0 || static_cast<size_t>(rround[r + 1]) + 32 * static_cast<size_t>(rround[r]) > rslab.size())
+        bad("reverse rounds");
+    for (size_t t = 0; t < S.tri_a.size(); ++t)
+      if (S.tri_a[t] < 0 || S.tri_a[t] >= nv || S.tri_b[t] < 0 || S.tri_b[t] >= nv) bad("triples");
+    for (int x : S.basis_idx)
+      if (x < 0 || x >= nv) bad("basis values");
   }
   std::vector<char> blob;
   const size_t o_tpk = put(blob, tri_pk), o_upk = put(blob, use_pk), o_cf = put(blob, coef_f);
@@ -605,6 +641,93 @@ mtp_status mtp_get_params(const mtp_model* md, double* theta, int64_t m) {
     check_model(md);
     if (!theta || m != md->sched.n_params) throw Fail{MTP_ERR_ARG, "theta size mismatch"};
     std::copy(md->theta.begin(), md->theta.end(), theta);
+  });
+}
+
+namespace {
+constexpr uint32_t kBlobMagic = 0x3150544du;   // "MTP1"
+constexpr uint32_t kBlobVersion = 1u;
+}  // namespace
+
+mtp_status mtp_save(const mtp_model* md, void* buffer, int64_t capacity, int64_t* size, void* stream) {
+  return guarded([&] {
+    check_model(md);
+    if (!size) throw Fail{MTP_ERR_ARG, "null size"};
+    const int64_t m = md->sched.n_params;
+    const bool with_a = md->have_ainv;
+    const int64_t need = 8 + static_cast<int64_t>(sizeof(mtp_desc)) + 8 + 8 * m + 8 + (with_a ? 8 * m * m : 0);
+    *size = need;
+    if (!buffer) return;
+    if (capacity < need) throw Fail{MTP_ERR_CAPACITY, "checkpoint needs " + std::to_string(need) + " bytes"};
+    unsigned char* p = static_cast<unsigned char*>(buffer);
+    auto put_bytes = [&](const void* src, size_t n) { std::memcpy(p, src, n); p += n; };
+    const uint32_t head[2] = {kBlobMagic, kBlobVersion};
+    put_bytes(head, 8);
+    put_bytes(&md->desc, sizeof(mtp_desc));
+    put_bytes(&m, 8);
+    put_bytes(md->theta.data(), 8 * m);
+    const int64_t flag = with_a ? 1 : 0;
+    put_bytes(&flag, 8);
+    if (with_a) {
+      MTP_CUDA(cudaMemcpyAsync(p, md->a_d.p, 8 * m * m, cudaMemcpyDeviceToHost, as_stream(stream)));
+      MTP_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    }
+  });
+}
+
+mtp_status mtp_restore(const void* buffer, int64_t size, mtp_model** out, void* stream) {
+  mtp_model* md = nullptr;
+  const mtp_status st = guarded([&] {
+    if (!buffer || !out) throw Fail{MTP_ERR_ARG, "null argument"};
+    if (size < 0) throw Fail{MTP_ERR_ARG, "negative size"};
+    const unsigned char* p = static_cast<const unsigned char*>(buffer);
+    const unsigned char* end = p + size;
+    auto get = [&](void* dst, size_t n) {
+      if (static_cast<size_t>(end - p) < n) throw Fail{MTP_ERR_ARG, "truncated checkpoint"};
+      std::memcpy(dst, p, n);
+      p += n;
+    };
+    uint32_t head[2];
+    get(head, 8);
+    if (head[0] != kBlobMagic || head[1] != kBlobVersion) throw Fail{MTP_ERR_ARG, "not an MTP checkpoint"};
+    mtp_desc d;
+    get(&d, sizeof(mtp_desc));
+    int64_t m = 0;
+    get(&m, 8);
+    if (m <= 0 || m > (1 << 20)) throw Fail{MTP_ERR_ARG, "bad parameter count"};
+    std::vector<double> theta(static_cast<size_t>(m));
+    get(theta.data(), 8 * m);
+    int64_t flag = 0;
+    get(&flag, 8);
+    std::vector<double> A;
+    if (flag) {
+      A.resize(static_cast<size_t>(m * m));
+      get(A.data(), 8 * m * m);
+    }
+    const mtp_status s1 = mtp_load(&d, theta.data(), m, &md);
+    if (s1 != MTP_OK) throw Fail{s1, mtp_last_error()};
+    if (flag) {
+      cudaStream_t s = as_stream(stream);
+      DevBuf dA;
+      dA.ensure(8 * m * m, s);
+      MTP_CUDA(cudaMemcpyAsync(dA.p, A.data(), 8 * m * m, cudaMemcpyHostToDevice, s));
+      const mtp_status s2 = mtp_set_active_set(md, dA.as<double>(), m, stream);
+      MTP_CUDA(cudaStreamSynchronize(s));
+      dA.release();
+      if (s2 != MTP_OK) throw Fail{s2, mtp_last_error()};
+    }
+    *out = md;
+  });
+  if (st != MTP_OK && md) mtp_free_model(md);
+  return st;
+}
+
+mtp_status mtp_debug_inject(int fault, int count) {
+  return guarded([&] {
+    if (count < 0) throw Fail{MTP_ERR_ARG, "negative count"};
+    if (fault == MTP_FAULT_DEVICE_ALLOC) g_inject_alloc = count;
+    else if (fault == MTP_FAULT_NEIGHBOR_OVERFLOW) g_inject_overflow = count;
+    else throw Fail{MTP_ERR_ARG, "unknown fault"};
   });
 }
 

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -228,6 +230,10 @@ void run_classify(const double* gamma, int64_t n, double g_save, double g_break,
 void run_widen_argmax(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
 int64_t run_cut_clusters(const mtp_batch* b, const int64_t* centers, int64_t n, double radius, int64_t* off,
                          double* pos, int32_t* type, int64_t* src, int64_t capacity, cudaStream_t s);
+// host-side fault injection (mtp_debug_inject): armed counts, each consumed by one event
+extern std::atomic<int> g_inject_alloc;
+extern std::atomic<int> g_inject_overflow;
+bool take_injected(std::atomic<int>& c);
 int64_t run_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_t max_swaps, int64_t* source,
                    cudaStream_t s);
 void run_grade(mtp_model* m, int64_t N, bool fp64, const double* rows, const float* rows_hi,

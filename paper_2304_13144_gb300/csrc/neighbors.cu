@@ -444,19 +444,26 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.pimg = nb->pimg.as<int>();
   A.pr32 = nb->pr32.as<float4>();
   A.prev = nb->prev.as<int>();
-  ProfRegion* pr2 = new ProfRegion("neighbors_fill_reverse", s);
-  k_pairs<true><<<blocks_for(N, 128), 128, 0, s>>>(A);
-  MTP_CUDA(cudaGetLastError());
-  if (total > 0) {
-    k_reverse<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
+  // fill (at the counted offsets) and reverse pairs; a fill that disagrees with its count sets
+  // ERRF_CAPACITY: the pass is repeated once, then the build fails with MTP_ERR_CAPACITY
+  for (int attempt = 0;; ++attempt) {
+    ProfRegion* pr2 = new ProfRegion("neighbors_fill_reverse", s);
+    k_pairs<true><<<blocks_for(N, 128), 128, 0, s>>>(A);
     MTP_CUDA(cudaGetLastError());
+    if (total > 0) {
+      k_reverse<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
+      MTP_CUDA(cudaGetLastError());
+    }
+    delete pr2;
+    MTP_CUDA(cudaMemcpyAsync(&flag, m->err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MTP_CUDA(cudaStreamSynchronize(s));
+    if (take_injected(g_inject_overflow)) flag |= ERRF_CAPACITY;
+    if (flag & ERRF_GEOMETRY) throw Fail{MTP_ERR_GEOMETRY, "coincident atoms (|r_ij| < 1e-8 A)"};
+    if (flag & ERRF_REVERSE) throw Fail{MTP_ERR_NUMERIC, "inconsistent neighbor list (reverse-pair mismatch)"};
+    if (!(flag & ERRF_CAPACITY)) break;
+    if (attempt == 1) throw Fail{MTP_ERR_CAPACITY, "neighbor fill overflowed its counted capacity twice"};
+    MTP_CUDA(cudaMemsetAsync(m->err_flag.p, 0, sizeof(unsigned), s));
   }
-  delete pr2;
-  MTP_CUDA(cudaMemcpyAsync(&flag, m->err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  MTP_CUDA(cudaStreamSynchronize(s));
-  if (flag & ERRF_GEOMETRY) throw Fail{MTP_ERR_GEOMETRY, "coincident atoms (|r_ij| < 1e-8 A)"};
-  if (flag & (ERRF_CAPACITY | ERRF_REVERSE))
-    throw Fail{MTP_ERR_NUMERIC, "inconsistent neighbor list (count/fill or reverse-pair mismatch)"};
   DevNbr& D = nb->dn;
   D.n_atoms = N;
   D.n_pairs = total;

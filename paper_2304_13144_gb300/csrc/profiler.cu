@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mtp_internal.h"
 #include "profiler.h"
 
@@ -38,6 +40,7 @@ cudaEvent_t take() {
 }  // namespace
 
 ProfRegion::ProfRegion(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  nvtxRangePushA(name);   // host-side range for timeline tools (a no-op without one attached)
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on) return;
   a_ = take();
@@ -46,6 +49,7 @@ ProfRegion::ProfRegion(const char* name, cudaStream_t s) : name_(name), s_(s) {
 }
 
 ProfRegion::~ProfRegion() {
+  nvtxRangePop();
   std::lock_guard<std::mutex> lk(g_mu);
   if (!a_ || !b_) return;
   cudaEventRecord(b_, s_);

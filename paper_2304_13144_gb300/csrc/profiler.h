@@ -4,7 +4,7 @@
 
 namespace mtp {
 // Records a CUDA event pair around the launches made during its lifetime, on stream s,
-// when tracing is enabled (mtp_profiler_enable).
+// when tracing is enabled (mtp_profiler_enable), and opens an NVTX range of the same name.
 class ProfRegion {
  public:
   ProfRegion(const char* name, cudaStream_t s);
