@@ -125,3 +125,51 @@ def test_b2_binary_16000_atoms_every_atom(api, prec):
         assert np.abs(out["energy"] - ref["E"]).max() / n <= 1e-6
         assert np.abs(out["forces"] - ref["F"]).max() <= 1e-5
         assert np.abs(out["virial"] - ref["W"]).max() <= 1e-5 * np.abs(ref["W"]).max()
+
+
+@pytest.fixture(scope="module")
+def c2_full(api):
+    """B2 binary 40^3 cells (128,000 atoms), level 16: the full-size mixed-vs-FP64 inference case."""
+    from paper_2304_13144_gb300 import configs
+    w = configs.workload("C2")
+    bnp = w.inputs()
+    theta = w.theta()
+    md = O.OracleModel(2, 16, 2.0, 5.0)
+    model = api.mtp_load(w.desc(), theta)
+    b = api.Batch(bnp)
+    nb = api.mtp_build_neighbors(model, b)
+    outs = {p: {k: v.cpu().numpy() for k, v in api.mtp_energy_forces_stress(model, b, nb, p).items()}
+            for p in ("mixed", "fp64")}
+    ref_nbr = O.batch_neighbors(bnp, 5.0, brute=False)
+    sample = synth.sample_atoms(222, len(bnp["type"]), 10)
+    needed = set(sample.tolist())
+    for k in sample:
+        needed.update(ref_nbr["j"][ref_nbr["off"][k]:ref_nbr["off"][k + 1]].tolist())
+    req = np.array(sorted(needed), np.int64)
+    s = O.sites(md, theta, bnp["type"], ref_nbr, req=req, want_dVdr=True)
+    pos_of = {int(a): q for q, a in enumerate(req)}
+    G = s["dVdr"]
+    F = np.zeros((len(sample), 3))
+    for q, k in enumerate(sample):
+        k = int(k)
+        F[q] += G[ref_nbr["off"][k]:ref_nbr["off"][k + 1]].sum(axis=0)
+        for j in set(ref_nbr["j"][ref_nbr["off"][k]:ref_nbr["off"][k + 1]].tolist()):
+            for p in range(ref_nbr["off"][j], ref_nbr["off"][j + 1]):
+                if ref_nbr["j"][p] == k:
+                    F[q] -= G[p]
+    V = s["V"][[pos_of[int(k)] for k in sample]]
+    return {"outs": outs, "sample": sample, "V": V, "F": F, "n": len(bnp["type"])}
+
+
+def test_b2_binary_128000_atoms_sampled_and_mixed_vs_fp64(c2_full):
+    k = c2_full["sample"]
+    o64, omx = c2_full["outs"]["fp64"], c2_full["outs"]["mixed"]
+    np.testing.assert_allclose(o64["site_energy"][k], c2_full["V"], rtol=1e-10,
+                               atol=1e-10 * np.abs(c2_full["V"]).max())
+    assert np.abs(o64["forces"][k] - c2_full["F"]).max() <= 1e-10 * max(1.0, np.abs(c2_full["F"]).max())
+    assert np.abs(omx["site_energy"][k] - c2_full["V"]).max() <= 1e-6
+    assert np.abs(omx["forces"][k] - c2_full["F"]).max() <= 1e-5
+    # every atom: the mixed path against the FP64 GPU path (itself pinned to the oracle above)
+    assert np.abs(omx["forces"] - o64["forces"]).max() <= 1e-5
+    assert np.abs(omx["energy"] - o64["energy"]).max() / c2_full["n"] <= 1e-6
+    assert np.abs(omx["virial"] - o64["virial"]).max() <= 1e-5 * np.abs(o64["virial"]).max()
