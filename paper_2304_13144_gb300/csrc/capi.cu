@@ -225,7 +225,7 @@ void upload_schedule(mtp_model* md) {
         std::vector<std::vector<uint32_t>> lists(32);
         for (int e = e0; e < e1; ++e)
           for (int u = use_ptr[rval[e]]; u < use_ptr[rval[e] + 1]; ++u) lists[e - e0].push_back(use_pk[u]);
-        const uint32_t gofs = static_cast<uint32_t>((nv + 3) & ~3);   // grads follow vals (padded) in shared memory
+        const uint32_t gofs = static_cast<uint32_t>(padded_nv(nv));   // grads follow vals in shared memory
         auto ord = bank_order(
             lists, L, [](uint32_t w) { return w & 4095u; }, [gofs](uint32_t w) { return gofs + ((w >> 12) & 4095u); },
             [](uint32_t w) { return w; });
@@ -233,15 +233,49 @@ void upload_schedule(mtp_model* md) {
           for (int l = 0; l < 32; ++l) rslab.push_back(it < static_cast<int>(ord[l].size()) ? ord[l][it] : pad);
       }
   }
+  // inline coefficients when every coefficient is m 2^e with m < 128 (as the multinomial
+  // weights of the contraction are) and the value indices fit 11 bits with the zero slot
+  bool coef_inline = false;
+  if (packable && nv + 1 <= 2048) {
+    std::vector<uint32_t> code(coef_f.size(), 0u);
+    bool ok = true;
+    for (size_t k = 0; k + 1 < coef_f.size(); ++k) {
+      const float c = coef_f[k];
+      uint32_t bits;
+      std::memcpy(&bits, &c, 4);
+      const int e8 = static_cast<int>((bits >> 23) & 255u);
+      if (!(c >= 1.0f) || static_cast<double>(c) != coefs[k] || (bits & 0x1FFFFu) != 0u || e8 > 127 + 15) {
+        ok = false;
+        break;
+      }
+      code[k] = (bits - 0x3F800000u) >> 17;   // 10 bits: exponent offset (4) and fraction (6)
+    }
+    if (ok) {
+      const uint32_t z = static_cast<uint32_t>(nv);   // the always-zero value slot
+      auto conv = [&](uint32_t w) {
+        const uint32_t ci = w >> 24;
+        if (ci == zero_ci) return z | (z << 11);     // 1 * 0 * 0
+        return (w & 4095u) | (((w >> 12) & 4095u) << 11) | (code[ci] << 22);
+      };
+      for (auto& w : fslab) w = conv(w);
+      for (auto& w : rslab) w = conv(w);
+      coef_inline = true;
+    }
+  }
   // every index the kernels will read from the schedule, checked on the host before upload
   {
     auto bad = [](const char* what) { throw Fail{MTP_ERR_NUMERIC, std::string("schedule index out of range: ") + what}; };
     const uint32_t ncf = static_cast<uint32_t>(coef_f.size());
     const uint32_t unv = static_cast<uint32_t>(nv);
-    for (uint32_t w : fslab)
-      if ((w & 4095u) >= unv || ((w >> 12) & 4095u) >= unv || (w >> 24) >= ncf) bad("forward slab");
-    for (uint32_t w : rslab)
-      if ((w & 4095u) >= unv || ((w >> 12) & 4095u) >= unv || (w >> 24) >= ncf) bad("reverse slab");
+    auto check_word = [&](uint32_t w, const char* what) {
+      if (coef_inline) {
+        if ((w & 2047u) > unv || ((w >> 11) & 2047u) > unv) bad(what);   // index nv = the zero slot
+      } else if ((w & 4095u) >= unv || ((w >> 12) & 4095u) >= unv || (w >> 24) >= ncf) {
+        bad(what);
+      }
+    };
+    for (uint32_t w : fslab) check_word(w, "forward slab");
+    for (uint32_t w : rslab) check_word(w, "reverse slab");
     for (int x : fr_dst)
       if (x != -1 && (x < nm || x >= nv)) bad("forward destinations");
     for (int x : rr_val)
@@ -292,6 +326,7 @@ void upload_schedule(mtp_model* md) {
   D.tri_pk = packable ? reinterpret_cast<const uint32_t*>(base + o_tpk) : nullptr;
   D.use_pk = packable ? reinterpret_cast<const uint32_t*>(base + o_upk) : nullptr;
   D.coef_f = reinterpret_cast<const float*>(base + o_cf);
+  D.coef_inline = coef_inline;
   D.n_coef = static_cast<int>(coef_f.size());
   D.n_tri = static_cast<int>(S.tri_a.size());
   D.fslab = reinterpret_cast<const uint32_t*>(base + o_fs);

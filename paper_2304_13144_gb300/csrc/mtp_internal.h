@@ -74,6 +74,10 @@ struct DevSchedule {
   const uint32_t* use_pk;
   const float* coef_f;
   int n_coef;
+  // slab words carry their coefficient inline: a | b << 11 | code << 22, with the float
+  // rebuilt as bits (code << 17) + 0x3F800000; padding terms read the always-zero value slot
+  // n_vals.  Otherwise a | b << 12 | ci << 24 with ci into coef_f (padding: coefficient 0).
+  bool coef_inline;
   int n_tri, n_use;         // lengths of the triple and use lists
   // "slab" form of the packed lists for warp-per-neighborhood execution: rounds of 32
   // destinations; word (round r, iteration it, lane l) at off_r + 32 it + l, lists padded to the
@@ -234,6 +238,9 @@ int64_t run_cut_clusters(const mtp_batch* b, const int64_t* centers, int64_t n, 
 extern std::atomic<int> g_inject_alloc;
 extern std::atomic<int> g_inject_overflow;
 bool take_injected(std::atomic<int>& c);
+// per-neighborhood value slots of the specialised kernel's shared-memory arrays: the values,
+// one always-zero slot (index n_values), padded to a multiple of 4
+inline int padded_nv(int n_values) { return (n_values + 1 + 3) & ~3; }
 int64_t run_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_t max_swaps, int64_t* source,
                    cudaStream_t s);
 void run_grade(mtp_model* m, int64_t N, bool fp64, const double* rows, const float* rows_hi,

@@ -495,66 +495,89 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
     float* v1 = valsA[1];
     float* g0 = gradsA[0];
     float* g1 = gradsA[1];
-    // ---------------- forward contraction (eqs. 5-6): both neighborhoods per term ----------------
-    for (int r = 0; r < d.n_fround; ++r) {
-      const int4 rd = s_fround[r];
-      const uint32_t* slab = s_fslab + rd.y + lane;
-      float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-      int it = 0;
-      for (; it + 2 <= rd.x; it += 2) {
-        const uint32_t w0 = FG ? __ldg(slab + 32 * it) : slab[32 * it];
-        const uint32_t w1 = FG ? __ldg(slab + 32 * it + 32) : slab[32 * it + 32];
-        const float c0 = coef[w0 >> 24], c1 = coef[w1 >> 24];
-        const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u, x1 = w1 & 4095u, y1 = (w1 >> 12) & 4095u;
-        a0 = fmaf(c0, v0[x0] * v0[y0], a0);
-        b0 = fmaf(c0, v1[x0] * v1[y0], b0);
-        a1 = fmaf(c1, v0[x1] * v0[y1], a1);
-        b1 = fmaf(c1, v1[x1] * v1[y1], b1);
+    // the contraction for one slab-word format (inline coefficient or coefficient table)
+    auto contract = [&](auto inl) {
+      constexpr bool INL = decltype(inl)::value;
+      auto decode = [&](uint32_t w, float& c, uint32_t& x, uint32_t& y) {
+        if constexpr (INL) {
+          c = __uint_as_float(((w >> 22) << 17) + 0x3F800000u);
+          x = w & 2047u;
+          y = (w >> 11) & 2047u;
+        } else {
+          c = coef[w >> 24];
+          x = w & 4095u;
+          y = (w >> 12) & 4095u;
+        }
+      };
+      // ---------------- forward contraction (eqs. 5-6): both neighborhoods per term ----------------
+      for (int r = 0; r < d.n_fround; ++r) {
+        const int4 rd = s_fround[r];
+        const uint32_t* slab = s_fslab + rd.y + lane;
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+        int it = 0;
+        for (; it + 2 <= rd.x; it += 2) {
+          const uint32_t w0 = FG ? __ldg(slab + 32 * it) : slab[32 * it];
+          const uint32_t w1 = FG ? __ldg(slab + 32 * it + 32) : slab[32 * it + 32];
+          float c0, c1;
+          uint32_t x0, y0, x1, y1;
+          decode(w0, c0, x0, y0);
+          decode(w1, c1, x1, y1);
+          a0 = fmaf(c0, v0[x0] * v0[y0], a0);
+          b0 = fmaf(c0, v1[x0] * v1[y0], b0);
+          a1 = fmaf(c1, v0[x1] * v0[y1], a1);
+          b1 = fmaf(c1, v1[x1] * v1[y1], b1);
+        }
+        if (it < rd.x) {
+          const uint32_t w0 = FG ? __ldg(slab + 32 * it) : slab[32 * it];
+          float c0;
+          uint32_t x0, y0;
+          decode(w0, c0, x0, y0);
+          a0 = fmaf(c0, v0[x0] * v0[y0], a0);
+          b0 = fmaf(c0, v1[x0] * v1[y0], b0);
+        }
+        const int dst = s_frdst[32 * r + lane];
+        if (dst >= 0) {
+          v0[dst] = a0 + a1;
+          v1[dst] = b0 + b1;
+        }
+        if (rd.z) __syncwarp();
       }
-      if (it < rd.x) {
-        const uint32_t w0 = FG ? __ldg(slab + 32 * it) : slab[32 * it];
-        const float c0 = coef[w0 >> 24];
-        const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u;
-        a0 = fmaf(c0, v0[x0] * v0[y0], a0);
-        b0 = fmaf(c0, v1[x0] * v1[y0], b0);
+      // ---------------- adjoint of the contraction (gather form): both neighborhoods ----------------
+      for (int r = 0; r < d.n_rround; ++r) {
+        const int4 rd = s_rround[r];
+        const uint32_t* slab = s_rslab + rd.y + lane;
+        const int x = s_rrval[32 * r + lane];
+        const float sd = x >= 0 ? s_seed[x] : 0.f;
+        float a0 = sd, a1 = 0.f, b0 = sd, b1 = 0.f;
+        int it = 0;
+        for (; it + 2 <= rd.x; it += 2) {
+          const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32];
+          float c0, c1;
+          uint32_t x0, y0, x1, y1;
+          decode(w0, c0, x0, y0);
+          decode(w1, c1, x1, y1);
+          a0 = fmaf(c0, v0[x0] * g0[y0], a0);
+          b0 = fmaf(c0, v1[x0] * g1[y0], b0);
+          a1 = fmaf(c1, v0[x1] * g0[y1], a1);
+          b1 = fmaf(c1, v1[x1] * g1[y1], b1);
+        }
+        if (it < rd.x) {
+          const uint32_t w0 = slab[32 * it];
+          float c0;
+          uint32_t x0, y0;
+          decode(w0, c0, x0, y0);
+          a0 = fmaf(c0, v0[x0] * g0[y0], a0);
+          b0 = fmaf(c0, v1[x0] * g1[y0], b0);
+        }
+        if (x >= 0) {
+          g0[x] = a0 + a1;
+          g1[x] = b0 + b1;
+        }
+        if (rd.z) __syncwarp();
       }
-      const int dst = s_frdst[32 * r + lane];
-      if (dst >= 0) {
-        v0[dst] = a0 + a1;
-        v1[dst] = b0 + b1;
-      }
-      if (rd.z) __syncwarp();
-    }
-    // ---------------- adjoint of the contraction (gather form): both neighborhoods ----------------
-    for (int r = 0; r < d.n_rround; ++r) {
-      const int4 rd = s_rround[r];
-      const uint32_t* slab = s_rslab + rd.y + lane;
-      const int x = s_rrval[32 * r + lane];
-      const float sd = x >= 0 ? s_seed[x] : 0.f;
-      float a0 = sd, a1 = 0.f, b0 = sd, b1 = 0.f;
-      int it = 0;
-      for (; it + 2 <= rd.x; it += 2) {
-        const uint32_t w0 = slab[32 * it], w1 = slab[32 * it + 32];
-        const float c0 = coef[w0 >> 24], c1 = coef[w1 >> 24];
-        const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u, x1 = w1 & 4095u, y1 = (w1 >> 12) & 4095u;
-        a0 = fmaf(c0, v0[x0] * g0[y0], a0);
-        b0 = fmaf(c0, v1[x0] * g1[y0], b0);
-        a1 = fmaf(c1, v0[x1] * g0[y1], a1);
-        b1 = fmaf(c1, v1[x1] * g1[y1], b1);
-      }
-      if (it < rd.x) {
-        const uint32_t w0 = slab[32 * it];
-        const float c0 = coef[w0 >> 24];
-        const uint32_t x0 = w0 & 4095u, y0 = (w0 >> 12) & 4095u;
-        a0 = fmaf(c0, v0[x0] * g0[y0], a0);
-        b0 = fmaf(c0, v1[x0] * g1[y0], b0);
-      }
-      if (x >= 0) {
-        g0[x] = a0 + a1;
-        g1[x] = b0 + b1;
-      }
-      if (rd.z) __syncwarp();
-    }
+    };
+    if (d.coef_inline) contract(std::true_type{});
+    else contract(std::false_type{});
     finish(wk0, i0, v0, g0, CBA[0]);
     if (two) finish(wk1, i1, v1, g1, CBA[1]);
   }
@@ -603,8 +626,9 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   P.NQ = d.n_q;
   P.CBN = d.n_types * d.n_rad * d.n_q;
   P.NC = d.n_types * P.CBN;
-  P.NV = (d.n_vals + 3) & ~3;
-  P.row_stage = o.rows_ld > 0 && o.rows_ld <= P.NV && (o.rows_ld & 3) == 0;
+  P.NV = padded_nv(d.n_vals);
+  // the staged row overwrites adjoint slots [0, ld): it must spare the zero slot n_vals
+  P.row_stage = o.rows_ld > 0 && o.rows_ld <= d.n_vals && (o.rows_ld & 3) == 0;
   P.c_bytes = (static_cast<size_t>(P.NC) * sizeof(float) + 15) & ~size_t(15);
   P.tab_bytes = ((256 + d.n_mom) * sizeof(float) + 15) & ~size_t(15);
   P.warp_bytes = ((4 * static_cast<size_t>(P.NV) + 32 * (d.n_rad + d.n_q) + 2 * P.CBN) * sizeof(float) +
