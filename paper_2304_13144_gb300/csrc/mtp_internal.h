@@ -186,6 +186,7 @@ struct mtp_nbr {
   int64_t n_atoms = 0, n_pairs = 0, n_cfg = 0;
   mtp::DevNbr dn{};
   mtp::DevBuf off, pj, pimg, prev, pr32, atom_cfg;
+  mtp::DevBuf segs;   // per-atom segment starts of the scanned bins (neighbors.cu)
   mtp::DevBuf bins, plan, shifts, wrap, scratch, counts;
   std::vector<mtp::CfgPlan> plans;
   std::vector<int64_t> atom_offset;   // host copy

@@ -59,6 +59,8 @@ struct NbrArgs {
   int* pimg;
   float4* pr32;
   int* prev;
+  uint16_t* seg;         // [n_atoms x kSegStride] start of each scanned bin's pairs in the atom's
+                         // list (relative), or null when a configuration scans more bins
   unsigned* err;
 };
 
@@ -185,6 +187,8 @@ __device__ __forceinline__ int decide(const NbrArgs& A, const DevCfg& C, int64_t
   return 1;
 }
 
+constexpr int kSegStride = 28;   // segment starts per atom: up to 27 scanned bins, then the end
+
 template <bool FILL>
 __global__ void k_pairs(NbrArgs A) {
   // threads take the atoms in bin order, so that a warp's atoms scan the same or adjacent bins
@@ -201,6 +205,12 @@ __global__ void k_pairs(NbrArgs A) {
   long long out = FILL ? A.off[i] : 0;
   const long long out_end = FILL ? A.off[i + 1] : 0;
   long long count = 0;
+  // segment starts: bins are scanned in increasing q = ((d0 + kb0) w1 + (d1 + kb1)) w2 + (d2 + kb2);
+  // skipped bins get empty segments
+  uint16_t* seg = (FILL && A.seg) ? A.seg + i * kSegStride : nullptr;
+  const int w1 = 2 * C.kb[1] + 1, w2 = 2 * C.kb[2] + 1;
+  const int n_scan = (2 * C.kb[0] + 1) * w1 * w2;
+  int q_next = 0;
   for (int d0 = -C.kb[0]; d0 <= C.kb[0]; ++d0) {
     int t0 = b0 + d0, n0 = 0;
     if (C.pbc[0]) { n0 = (t0 >= 0) ? t0 / C.nb[0] : -((-t0 + C.nb[0] - 1) / C.nb[0]); t0 -= n0 * C.nb[0]; }
@@ -213,6 +223,10 @@ __global__ void k_pairs(NbrArgs A) {
         int t2 = b2 + d2, n2 = 0;
         if (C.pbc[2]) { n2 = (t2 >= 0) ? t2 / C.nb[2] : -((-t2 + C.nb[2] - 1) / C.nb[2]); t2 -= n2 * C.nb[2]; }
         else if (t2 < 0 || t2 >= C.nb[2]) continue;
+        if (seg) {
+          const int q = ((d0 + C.kb[0]) * w1 + (d1 + C.kb[1])) * w2 + (d2 + C.kb[2]);
+          for (; q_next <= q; ++q_next) seg[q_next] = static_cast<uint16_t>(count);
+        }
         const long long tb = C.bin_base + (static_cast<long long>(t0) * C.nb[1] + t1) * C.nb[2] + t2;
         const long long s0 = A.bin_start[tb], s1 = A.bin_start[tb + 1];
         for (long long s = s0; s < s1; ++s) {
@@ -234,12 +248,16 @@ __global__ void k_pairs(NbrArgs A) {
       }
     }
   }
+  if (seg)
+    for (; q_next <= n_scan; ++q_next) seg[q_next] = static_cast<uint16_t>(count);
   if (!FILL) A.cnt[i] = count;
   else if (count != out_end - A.off[i]) atomicOr(A.err, ERRF_CAPACITY);
 }
 
 // prev[p] = index of the reverse pair (j -> i, -image) of pair p = (i -> j, image): one warp
-// per atom i (its pairs over the lanes), each lane scanning j's list.
+// per atom i (its pairs over the lanes).  The bin scan order is point-symmetric: a pair found
+// in i's q-th scanned bin is found from j in j's (n_scan - 1 - q)-th, so with segment starts
+// only that segment of j's list is searched (the whole list otherwise, or as a fallback).
 __global__ void k_reverse(NbrArgs A) {
   const int lane = threadIdx.x & 31;
   const long long wpb = blockDim.x >> 5;
@@ -251,9 +269,29 @@ __global__ void k_reverse(NbrArgs A) {
       const int img = A.pimg[p];
       const int want = pack_img(-unpack_img(img, 0), -unpack_img(img, 1), -unpack_img(img, 2));
       int found = -1;
-      const long long q1 = A.off[j + 1];
-      for (long long q = A.off[j]; q < q1; ++q)
-        if (A.pj[q] == static_cast<int>(i) && A.pimg[q] == want) { found = static_cast<int>(q); break; }
+      const long long oj = A.off[j];
+      if (A.seg) {
+        const DevCfg& C = A.cfg[A.atom_cfg[i]];
+        const int n_scan = (2 * C.kb[0] + 1) * (2 * C.kb[1] + 1) * (2 * C.kb[2] + 1);
+        const uint16_t* si = A.seg + i * kSegStride;
+        const int rel = static_cast<int>(p - A.off[i]);
+        int lo = 0, hi = n_scan - 1;   // the last q with si[q] <= rel
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (si[mid] <= rel) lo = mid; else hi = mid - 1;
+        }
+        const int qm = n_scan - 1 - lo;
+        const uint16_t* sj = A.seg + static_cast<long long>(j) * kSegStride;
+        const long long oj1 = A.off[j + 1];
+        const long long e1 = min(oj + sj[qm + 1], oj1);
+        for (long long q = min(oj + sj[qm], oj1); q < e1; ++q)
+          if (A.pj[q] == static_cast<int>(i) && A.pimg[q] == want) { found = static_cast<int>(q); break; }
+      }
+      if (found < 0) {
+        const long long q1 = A.off[j + 1];
+        for (long long q = oj; q < q1; ++q)
+          if (A.pj[q] == static_cast<int>(i) && A.pimg[q] == want) { found = static_cast<int>(q); break; }
+      }
       if (found < 0) atomicOr(A.err, ERRF_REVERSE);
       A.prev[p] = found < 0 ? static_cast<int>(p) : found;
     }
@@ -444,6 +482,17 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.pimg = nb->pimg.as<int>();
   A.pr32 = nb->pr32.as<float4>();
   A.prev = nb->prev.as<int>();
+  A.seg = nullptr;
+  {
+    int max_scan = 0;
+    for (const DevCfg& C : cfgs) max_scan = std::max(max_scan, (2 * C.kb[0] + 1) * (2 * C.kb[1] + 1) * (2 * C.kb[2] + 1));
+    // the hints are 16-bit offsets into an atom's list; the search clamps them to the list, so a
+    // list longer than 65535 pairs only loses the hint (the whole list is searched)
+    if (max_scan < kSegStride) {
+      nb->segs.ensure(static_cast<size_t>(std::max<int64_t>(N, 1)) * kSegStride * sizeof(uint16_t), s);
+      A.seg = nb->segs.as<uint16_t>();
+    }
+  }
   // fill (at the counted offsets) and reverse pairs; a fill that disagrees with its count sets
   // ERRF_CAPACITY: the pass is repeated once, then the build fails with MTP_ERR_CAPACITY
   for (int attempt = 0;; ++attempt) {
