@@ -128,10 +128,29 @@ struct TcArgs {
   int n_pass;          // ld / BN
   int k_chunks;        // ld / BK
   int64_t n_tiles;     // ceil(N / BM)
-  double* gamma;
-  int32_t* argmax;
+  int64_t n_work;      // n_tiles * n_pass work items (tile, pass)
+  float* pbest;        // [n_pass x N] per-pass row maxima
+  int32_t* parg;       // [n_pass x N] and their columns
   unsigned* err;
 };
+
+// gamma_i and argmax_i from the per-pass partials: passes in column order, strict '>' keeps the
+// lowest column on ties; a NaN partial (a pass that did not run) makes gamma_i NaN
+__global__ void k_grade_combine(int64_t N, int n_pass, const float* pbest, const int32_t* parg, double* gamma,
+                                int32_t* argmax) {
+  const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (r >= N) return;
+  float best = -1.f;
+  int arg = 0;
+  bool nan = false;
+  for (int p = 0; p < n_pass; ++p) {
+    const float v = pbest[p * N + r];
+    nan = nan || (v != v);
+    if (v > best) { best = v; arg = parg[p * N + r]; }
+  }
+  gamma[r] = nan ? __longlong_as_double(0x7ff8000000000000LL) : static_cast<double>(best);
+  if (argmax) argmax[r] = arg;
+}
 
 __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__ CUtensorMap mAh,
                                                           const __grid_constant__ CUtensorMap mAl,
@@ -170,8 +189,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
   if (warp == 0) {
     if (lane == 0) {
       uint32_t it = 0;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && !*abort_flag; tile += gridDim.x)
-        for (int pass = 0; pass < a.n_pass && !*abort_flag; ++pass)
+      // work item w = (tile w / n_pass, pass w % n_pass); the grid is a multiple of n_pass, so the
+      // CTAs of one tile run its passes side by side (the row tile is read from DRAM once) and
+      // each CTA keeps one column slab of A^-1
+      for (int64_t w = blockIdx.x; w < a.n_work && !*abort_flag; w += gridDim.x) {
+        const int64_t tile = w / a.n_pass;
+        const int pass = static_cast<int>(w - tile * a.n_pass);
           for (int kc = 0; kc < a.k_chunks; ++kc, ++it) {
             const uint32_t s = it % STAGES, n = it / STAGES;
             if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag)) { *abort_flag = 1; break; }
@@ -183,6 +206,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
             tma_load_2d(st + 2 * A_BYTES, &mBh, x, yc, &full[s]);
             tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBl, x, yc, &full[s]);
           }
+      }
       if (*abort_flag) {
         // let the copies already issued land before the CTA's shared memory goes away
         for (uint32_t j = (it > STAGES ? it - STAGES : 0); j < it; ++j) {
@@ -197,8 +221,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
                              (static_cast<uint32_t>(BM >> 4) << 24);
       uint32_t it = 0, acc_it = 0;
       bool issued = false;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && !*abort_flag; tile += gridDim.x)
-        for (int pass = 0; pass < a.n_pass && !*abort_flag; ++pass, ++acc_it) {
+      for (int64_t w = blockIdx.x; w < a.n_work && !*abort_flag; w += gridDim.x, ++acc_it) {
+        {
           const uint32_t b = acc_it & 1, na = acc_it >> 1;
           if (na > 0 && !mbar_wait(&acce[b], (na - 1) & 1, abort_flag)) { *abort_flag = 1; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -223,6 +247,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
           if (*abort_flag) break;
           mma_commit(&accf[b]);
         }
+      }
       if (issued) {
         // all MMAs of this thread complete before TMEM is released
         mma_commit(drain);
@@ -234,11 +259,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
   } else {
     const int q = warp & 3;   // TMEM lane quarter accessible to this warp
     uint32_t acc_it = 0;
-    for (int64_t tile = blockIdx.x; tile < a.n_tiles && !*abort_flag; tile += gridDim.x) {
+    for (int64_t w = blockIdx.x; w < a.n_work && !*abort_flag; w += gridDim.x) {
+      const int64_t tile = w / a.n_pass;
+      const int pass = static_cast<int>(w - tile * a.n_pass);
       float best = -1.f;
       int barg = 0;
-      for (int pass = 0; pass < a.n_pass; ++pass, ++acc_it) {
+      {
         const uint32_t b = acc_it & 1, na = acc_it >> 1;
+        ++acc_it;
         bool ok = true;
         if (lane == 0) ok = mbar_wait(&accf[b], na & 1, abort_flag);
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
@@ -263,8 +291,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
       if (*abort_flag) break;
       const int64_t row = tile * BM + q * 32 + lane;
       if (row < a.N) {
-        a.gamma[row] = static_cast<double>(best);
-        if (a.argmax) a.argmax[row] = barg;
+        a.pbest[pass * a.N + row] = best;
+        a.parg[pass * a.N + row] = barg;
       }
     }
   }
@@ -335,15 +363,22 @@ void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, in
   a.n_pass = static_cast<int>(ld / BN);
   a.k_chunks = static_cast<int>(ld / BK);
   a.n_tiles = (N + BM - 1) / BM;
-  a.gamma = gamma;
-  a.argmax = argmax;
+  a.n_work = a.n_tiles * a.n_pass;
+  md->ws_grade.ensure(static_cast<size_t>(a.n_pass) * N * (sizeof(float) + sizeof(int32_t)), s);
+  a.pbest = md->ws_grade.as<float>();
+  a.parg = reinterpret_cast<int32_t*>(a.pbest + static_cast<size_t>(a.n_pass) * N);
+  // partials start as NaN: a pass that does not run (a bounded wait expired) leaves gamma NaN
+  MTP_CUDA(cudaMemsetAsync(a.pbest, 0xFF, static_cast<size_t>(a.n_pass) * N * sizeof(float), s));
   a.err = md->err_flag.as<unsigned>();
   MTP_CUDA(cudaFuncSetAttribute(k_grade_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SMEM_BYTES)));
   int nsm = 0;
   MTP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, md->device));
-  const int grid = static_cast<int>(std::min<int64_t>(a.n_tiles, nsm));
+  const int per = nsm >= a.n_pass ? (nsm / a.n_pass) * a.n_pass : nsm;   // a multiple of n_pass
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(a.n_work, per)));
   ProfRegion pr("grade_tc_tf32x3", s);
   k_grade_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, a);
+  MTP_CUDA(cudaGetLastError());
+  k_grade_combine<<<static_cast<unsigned>((N + 255) / 256), 256, 0, s>>>(N, a.n_pass, a.pbest, a.parg, gamma, argmax);
   MTP_CUDA(cudaGetLastError());
 }
 

@@ -167,6 +167,7 @@ struct mtp_model {
   mtp::DevBuf ws_pair;         // per-pair gradients
   mtp::DevBuf ws_atom;         // per-atom V, W
   mtp::DevBuf ws_rows;         // parameter rows for the grade
+  mtp::DevBuf ws_grade;        // per-pass partial row maxima of the tensor-core grade
   mtp::DevBuf ws_misc;
   mtp::DevBuf ws_red;          // reductions
   mtp::DevBuf err_flag;        // unsigned
