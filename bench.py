@@ -48,8 +48,8 @@ MEASURED_TRAFFIC = {
                       "sha1": "3d00184d3db4919a4d57decafab6ea05a70dc54b",
                       "atoms": 131072, "bytes": 120069376 + 724567040},
     "grade_tc_tf32x3": {"source": "paper_2304_13144_gb300/csrc/grade_tc.cu",
-                        "sha1": "deb84dffd40a2d3a7df80df8ef1b1ff027f62c1c",
-                        "atoms": 131072, "bytes": 1848208640 + 1337600},
+                        "sha1": "edc8f658b225b15351d41bea8a0a3621a776d4a4",
+                        "atoms": 131072, "bytes": 708316672 + 2827776},
 }
 
 

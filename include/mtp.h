@@ -198,7 +198,8 @@ mtp_status mtp_param_rows(mtp_model* model, const mtp_batch* batch, const mtp_nb
  * DEVICE outputs: gamma[N] (FP64), argmax[N] or NULL, flagged[N] or NULL,
  * n_flagged[1] (int64) or NULL.  Requires mtp_set_active_set.  MTP_MIXED forms the
  * product with split-precision tensor-core arithmetic (FP32-level accuracy); MTP_FP64
- * in FP64. */
+ * in FP64.  Every wait inside the tensor-core kernel is bounded: if one expires, the kernel
+ * stops, and the gamma_i it did not finish are NaN (never flagged). */
 mtp_status mtp_grade(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
                      mtp_precision prec, double threshold, double* gamma, int32_t* argmax,
                      int32_t* flagged, int64_t* n_flagged, void* stream);
