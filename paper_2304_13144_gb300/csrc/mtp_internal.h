@@ -188,6 +188,7 @@ struct mtp_nbr {
   mtp::DevNbr dn{};
   mtp::DevBuf off, pj, pimg, prev, pr32, atom_cfg;
   mtp::DevBuf segs;   // per-atom segment starts of the scanned bins (neighbors.cu)
+  mtp::DevBuf masks;  // per-atom accepted-candidate bits of the count pass (neighbors.cu)
   mtp::DevBuf bins, plan, shifts, wrap, scratch, counts;
   std::vector<mtp::CfgPlan> plans;
   std::vector<int64_t> atom_offset;   // host copy

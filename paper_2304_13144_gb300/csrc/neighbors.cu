@@ -61,6 +61,8 @@ struct NbrArgs {
   int* prev;
   uint16_t* seg;         // [n_atoms x kSegStride] start of each scanned bin's pairs in the atom's
                          // list (relative), or null when a configuration scans more bins
+  uint32_t* mask;        // [kMaskWords x n_atoms] accepted bits of the atom's first kMaskBits
+                         // candidates in scan order (count pass writes, fill pass reads)
   unsigned* err;
 };
 
@@ -188,6 +190,8 @@ __device__ __forceinline__ int decide(const NbrArgs& A, const DevCfg& C, int64_t
 }
 
 constexpr int kSegStride = 28;   // segment starts per atom: up to 27 scanned bins, then the end
+constexpr int kMaskWords = 16;   // accepted-candidate bits per atom recorded by the count pass
+constexpr int kMaskBits = 32 * kMaskWords;
 
 template <bool FILL>
 __global__ void k_pairs(NbrArgs A) {
@@ -205,6 +209,8 @@ __global__ void k_pairs(NbrArgs A) {
   long long out = FILL ? A.off[i] : 0;
   const long long out_end = FILL ? A.off[i + 1] : 0;
   long long count = 0;
+  int cand = 0;          // candidate index in scan order (the self candidate included)
+  uint32_t mword = 0;    // count pass: accepted bits of the current mask word
   // segment starts: bins are scanned in increasing q = ((d0 + kb0) w1 + (d1 + kb1)) w2 + (d2 + kb2);
   // skipped bins get empty segments
   uint16_t* seg = (FILL && A.seg) ? A.seg + i * kSegStride : nullptr;
@@ -229,20 +235,48 @@ __global__ void k_pairs(NbrArgs A) {
         }
         const long long tb = C.bin_base + (static_cast<long long>(t0) * C.nb[1] + t1) * C.nb[2] + t2;
         const long long s0 = A.bin_start[tb], s1 = A.bin_start[tb + 1];
-        for (long long s = s0; s < s1; ++s) {
+        // candidate s of this bin: 1 if (i -> j, n) is a pair (written out in the fill pass)
+        auto test = [&](long long s) -> int {
           const float4 xj_h = A.bph[s];
           const int j = __float_as_int(xj_h.w);
-          if (j == static_cast<int>(i) && n0 == 0 && n1 == 0 && n2 == 0) continue;
+          if (j == static_cast<int>(i) && n0 == 0 && n1 == 0 && n2 == 0) return 0;
           float4 r;
           int img;
-          if (decide(A, C, i, j, xi_h, xi_l, xj_h, A.bpl[s], n0, n1, n2, r, img)) {
-            if (FILL && out < out_end) {
-              A.pj[out] = j;
-              A.pimg[out] = img;
-              A.pr32[out] = r;
-              ++out;
+          if (!decide(A, C, i, j, xi_h, xi_l, xj_h, A.bpl[s], n0, n1, n2, r, img)) return 0;
+          if (FILL && out < out_end) {
+            A.pj[out] = j;
+            A.pimg[out] = img;
+            A.pr32[out] = r;
+            ++out;
+          }
+          ++count;
+          return 1;
+        };
+        long long s = s0;
+        if (FILL && A.mask) {
+          // replay the count pass's decisions: only its accepted candidates are formed again
+          while (s < s1 && cand < kMaskBits) {
+            const int wb = cand & 31;
+            const int span = static_cast<int>(min(static_cast<long long>(32 - wb), s1 - s));
+            uint32_t word = A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + i] >> wb;
+            if (span < 32) word &= (1u << span) - 1u;
+            while (word) {
+              const int b = __ffs(word) - 1;
+              word &= word - 1u;
+              test(s + b);
             }
-            ++count;
+            s += span;
+            cand += span;
+          }
+        }
+        for (; s < s1; ++s, ++cand) {
+          const int acc = test(s);
+          if (!FILL && A.mask && cand < kMaskBits) {
+            mword |= static_cast<uint32_t>(acc) << (cand & 31);
+            if ((cand & 31) == 31) {
+              A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + i] = mword;
+              mword = 0;
+            }
           }
         }
       }
@@ -250,6 +284,8 @@ __global__ void k_pairs(NbrArgs A) {
   }
   if (seg)
     for (; q_next <= n_scan; ++q_next) seg[q_next] = static_cast<uint16_t>(count);
+  if (!FILL && A.mask && cand < kMaskBits && (cand & 31) != 0)
+    A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + i] = mword;
   if (!FILL) A.cnt[i] = count;
   else if (count != out_end - A.off[i]) atomicOr(A.err, ERRF_CAPACITY);
 }
@@ -442,6 +478,8 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.cnt = nb->counts.as<long long>();
   A.off = nb->off.as<long long>();
   A.err = m->err_flag.as<unsigned>();
+  nb->masks.ensure(static_cast<size_t>(N) * kMaskWords * sizeof(uint32_t), s);
+  A.mask = nb->masks.as<uint32_t>();
   const int TB = 256;
   ProfRegion* pr1 = new ProfRegion("neighbors_bin_count", s);
   k_prep<<<blocks_for(N, TB), TB, 0, s>>>(A);

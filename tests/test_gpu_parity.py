@@ -96,10 +96,17 @@ def check_efs(out, ref, n_atoms, prec):
 # neighborhoods
 # ---------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["fcc108", "triclinic_mixed_pbc", "tiny_cell", "open"])
+@pytest.mark.parametrize("case", ["fcc108", "triclinic_mixed_pbc", "tiny_cell", "open", "dense_random"])
 def test_neighbor_list_matches_oracle(api, case):
     if case == "fcc108":
         bnp = synth.fcc_unary_108()
+    elif case == "dense_random":
+        # 800 uniform atoms in a 13 A periodic cube: 2 bins per axis, 27 scanned bins per atom and
+        # about 2,700 candidates each (the count pass records the first 512 decisions; the fill
+        # pass decides the rest again)
+        g = synth.rng(18)
+        cell = 13.0 * np.eye(3)
+        bnp = synth.single(g.uniform(0, 13.0, (800, 3)), np.zeros(800, np.int32), cell)
     elif case == "tiny_cell":
         bnp = small_cfg(3, "bcc", (1, 1, 2), 1)
     else:
