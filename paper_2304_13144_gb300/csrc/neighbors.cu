@@ -30,6 +30,8 @@ struct DevCfg {
   long long bin_base, shift_base;
   float rc2f, rcm2f;
   double rc2;
+  float rcf;    // R_cut in FP32
+  float smax;   // largest |component| of the configuration's image shifts (FP32 high parts)
 };
 
 struct NbrArgs {
@@ -46,7 +48,7 @@ struct NbrArgs {
   int* wrap;             // packed integer wrap of each atom
   long long* atom_bin;   // global bin of each atom
   float4* ph;            // wrapped position hi (.w = atom index bits)
-  float4* pl;            // wrapped position lo
+  float4* pl;            // wrapped position lo (.w = packed wrap of the atom)
   int* bin_count;
   int* bin_fill;
   long long* bin_start;  // [n_bins + 1]
@@ -61,9 +63,11 @@ struct NbrArgs {
   int* prev;
   uint16_t* seg;         // [n_atoms x kSegStride] start of each scanned bin's pairs in the atom's
                          // list (relative), or null when a configuration scans more bins
-  uint32_t* mask;        // [kMaskWords x n_atoms] accepted bits of the atom's first kMaskBits
-                         // candidates in scan order (count pass writes, fill pass reads)
+  uint8_t* pq;           // per pair: index of the scanned bin it was found in (with seg)
+  uint32_t* mask;        // [kMaskWords x n_atoms] accepted bits of the first kMaskBits candidates
+                         // in scan order, by bin-order position (count pass writes, fill reads)
   unsigned* err;
+  unsigned* xmax;        // bits of the largest |component| of any wrapped position (FP32 high parts)
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -105,13 +109,20 @@ __global__ void k_prep(NbrArgs A) {
     int bi = static_cast<int>(floor(s * C.nb[a]));
     b[a] = min(max(bi, 0), C.nb[a] - 1);
   }
-  A.wrap[i] = pack_img(w[0], w[1], w[2]);
+  const int wpk = pack_img(w[0], w[1], w[2]);
+  A.wrap[i] = wpk;
   double xw[3];
   for (int c = 0; c < 3; ++c) xw[c] = x[c] - (w[0] * C.H[0 * 3 + c] + w[1] * C.H[1 * 3 + c] + w[2] * C.H[2 * 3 + c]);
   float h[3], l[3];
   for (int c = 0; c < 3; ++c) { h[c] = __double2float_rn(xw[c]); l[c] = __double2float_rn(xw[c] - static_cast<double>(h[c])); }
   A.ph[i] = make_float4(h[0], h[1], h[2], __int_as_float(static_cast<int>(i)));
-  A.pl[i] = make_float4(l[0], l[1], l[2], 0.f);
+  {
+    // non-negative floats order like their bit patterns: one atomic per warp
+    const unsigned hb = __float_as_uint(fmaxf(fabsf(h[0]), fmaxf(fabsf(h[1]), fabsf(h[2]))));
+    const unsigned wm = __reduce_max_sync(__activemask(), hb);
+    if (hb == wm) atomicMax(A.xmax, wm);
+  }
+  A.pl[i] = make_float4(l[0], l[1], l[2], __int_as_float(wpk));   // .w: the packed wrap
   long long bin = C.bin_base + (static_cast<long long>(b[0]) * C.nb[1] + b[1]) * C.nb[2] + b[2];
   A.atom_bin[i] = bin;
   atomicAdd(&A.bin_count[bin], 1);
@@ -164,7 +175,7 @@ __device__ __forceinline__ int decide(const NbrArgs& A, const DevCfg& C, int64_t
     r[c] = __fadd_rn(s2, low);
   }
   const float d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-  const int wi = A.wrap[i], wj = A.wrap[j];
+  const int wi = __float_as_int(xi_l.w), wj = __float_as_int(xj_l.w);   // packed wraps
   const int m0 = n0 - unpack_img(wj, 0) + unpack_img(wi, 0);
   const int m1 = n1 - unpack_img(wj, 1) + unpack_img(wi, 1);
   const int m2 = n2 - unpack_img(wj, 2) + unpack_img(wi, 2);
@@ -209,6 +220,18 @@ __global__ void k_pairs(NbrArgs A) {
   long long out = FILL ? A.off[i] : 0;
   const long long out_end = FILL ? A.off[i + 1] : 0;
   long long count = 0;
+  // count pass: a candidate whose FP32 estimate |a|, a = (x_j - x_i) + shift (high parts), is
+  // below t_fast is a pair without forming r_ij.  |a - r_ij| <= b per component with
+  // b = 2^-24 (4 X + 2 S + R_cut) (X, S: largest wrapped-position and shift components), so
+  // |a|^2 < (R_cut (1 - 1e-5) - 2 b)^2 puts r_ij^2 below R_cut^2 (1 - 1.6e-5): outside the
+  // band that decide() settles in FP64, on the accepting side.  |a|^2 > 1e-6 keeps coincident
+  // atoms on the full path.
+  float t_fast = 0.f;
+  if (!FILL) {
+    const float b = 5.9604645e-8f * 1.1f * (4.f * __uint_as_float(*A.xmax) + 2.f * C.smax + C.rcf);
+    const float rr = C.rcf * (1.f - 1e-5f) - 2.f * b;
+    if (b < 1e-4f && rr > 0.f) t_fast = rr * rr;
+  }
   int cand = 0;          // candidate index in scan order (the self candidate included)
   uint32_t mword = 0;    // count pass: accepted bits of the current mask word
   // segment starts: bins are scanned in increasing q = ((d0 + kb0) w1 + (d1 + kb1)) w2 + (d2 + kb2);
@@ -219,27 +242,39 @@ __global__ void k_pairs(NbrArgs A) {
   int q_next = 0;
   for (int d0 = -C.kb[0]; d0 <= C.kb[0]; ++d0) {
     int t0 = b0 + d0, n0 = 0;
-    if (C.pbc[0]) { n0 = (t0 >= 0) ? t0 / C.nb[0] : -((-t0 + C.nb[0] - 1) / C.nb[0]); t0 -= n0 * C.nb[0]; }
+    if (C.pbc[0]) {
+        if (t0 < 0 || t0 >= C.nb[0]) { n0 = (t0 >= 0) ? t0 / C.nb[0] : -((-t0 + C.nb[0] - 1) / C.nb[0]); t0 -= n0 * C.nb[0]; }
+      }
     else if (t0 < 0 || t0 >= C.nb[0]) continue;
     for (int d1 = -C.kb[1]; d1 <= C.kb[1]; ++d1) {
       int t1 = b1 + d1, n1 = 0;
-      if (C.pbc[1]) { n1 = (t1 >= 0) ? t1 / C.nb[1] : -((-t1 + C.nb[1] - 1) / C.nb[1]); t1 -= n1 * C.nb[1]; }
+      if (C.pbc[1]) {
+        if (t1 < 0 || t1 >= C.nb[1]) { n1 = (t1 >= 0) ? t1 / C.nb[1] : -((-t1 + C.nb[1] - 1) / C.nb[1]); t1 -= n1 * C.nb[1]; }
+      }
       else if (t1 < 0 || t1 >= C.nb[1]) continue;
       for (int d2 = -C.kb[2]; d2 <= C.kb[2]; ++d2) {
         int t2 = b2 + d2, n2 = 0;
-        if (C.pbc[2]) { n2 = (t2 >= 0) ? t2 / C.nb[2] : -((-t2 + C.nb[2] - 1) / C.nb[2]); t2 -= n2 * C.nb[2]; }
+        if (C.pbc[2]) {
+        if (t2 < 0 || t2 >= C.nb[2]) { n2 = (t2 >= 0) ? t2 / C.nb[2] : -((-t2 + C.nb[2] - 1) / C.nb[2]); t2 -= n2 * C.nb[2]; }
+      }
         else if (t2 < 0 || t2 >= C.nb[2]) continue;
-        if (seg) {
-          const int q = ((d0 + C.kb[0]) * w1 + (d1 + C.kb[1])) * w2 + (d2 + C.kb[2]);
+        const int q = ((d0 + C.kb[0]) * w1 + (d1 + C.kb[1])) * w2 + (d2 + C.kb[2]);
+        if (seg)
           for (; q_next <= q; ++q_next) seg[q_next] = static_cast<uint16_t>(count);
-        }
         const long long tb = C.bin_base + (static_cast<long long>(t0) * C.nb[1] + t1) * C.nb[2] + t2;
         const long long s0 = A.bin_start[tb], s1 = A.bin_start[tb + 1];
+        const float4 sh_b = A.sh_hi[C.shift_base + ((static_cast<long long>(n0 + C.K) * (2 * C.K + 1) + (n1 + C.K)) * (2 * C.K + 1) + (n2 + C.K))];
         // candidate s of this bin: 1 if (i -> j, n) is a pair (written out in the fill pass)
         auto test = [&](long long s) -> int {
           const float4 xj_h = A.bph[s];
           const int j = __float_as_int(xj_h.w);
           if (j == static_cast<int>(i) && n0 == 0 && n1 == 0 && n2 == 0) return 0;
+          if (!FILL) {
+            const float ax = (xj_h.x - xi_h.x) + sh_b.x, ay = (xj_h.y - xi_h.y) + sh_b.y, az = (xj_h.z - xi_h.z) + sh_b.z;
+            const float q = ax * ax + ay * ay + az * az;
+            if (q > C.rcm2f) return 0;
+            if (q < t_fast && q > 1e-6f) { ++count; return 1; }
+          }
           float4 r;
           int img;
           if (!decide(A, C, i, j, xi_h, xi_l, xj_h, A.bpl[s], n0, n1, n2, r, img)) return 0;
@@ -247,6 +282,7 @@ __global__ void k_pairs(NbrArgs A) {
             A.pj[out] = j;
             A.pimg[out] = img;
             A.pr32[out] = r;
+            if (seg) A.pq[out] = static_cast<uint8_t>(q);
             ++out;
           }
           ++count;
@@ -258,7 +294,7 @@ __global__ void k_pairs(NbrArgs A) {
           while (s < s1 && cand < kMaskBits) {
             const int wb = cand & 31;
             const int span = static_cast<int>(min(static_cast<long long>(32 - wb), s1 - s));
-            uint32_t word = A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + i] >> wb;
+            uint32_t word = A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + t] >> wb;
             if (span < 32) word &= (1u << span) - 1u;
             while (word) {
               const int b = __ffs(word) - 1;
@@ -274,7 +310,7 @@ __global__ void k_pairs(NbrArgs A) {
           if (!FILL && A.mask && cand < kMaskBits) {
             mword |= static_cast<uint32_t>(acc) << (cand & 31);
             if ((cand & 31) == 31) {
-              A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + i] = mword;
+              A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + t] = mword;
               mword = 0;
             }
           }
@@ -285,7 +321,7 @@ __global__ void k_pairs(NbrArgs A) {
   if (seg)
     for (; q_next <= n_scan; ++q_next) seg[q_next] = static_cast<uint16_t>(count);
   if (!FILL && A.mask && cand < kMaskBits && (cand & 31) != 0)
-    A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + i] = mword;
+    A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + t] = mword;
   if (!FILL) A.cnt[i] = count;
   else if (count != out_end - A.off[i]) atomicOr(A.err, ERRF_CAPACITY);
 }
@@ -302,6 +338,11 @@ __global__ void k_reverse(NbrArgs A) {
     const long long p1 = A.off[i + 1];
     for (long long p = A.off[i] + lane; p < p1; p += 32) {
       const int j = A.pj[p];
+      if (j < 0 || j >= A.n_atoms) {   // a list that disagrees with its count
+        atomicOr(A.err, ERRF_REVERSE);
+        A.prev[p] = static_cast<int>(p);
+        continue;
+      }
       const int img = A.pimg[p];
       const int want = pack_img(-unpack_img(img, 0), -unpack_img(img, 1), -unpack_img(img, 2));
       int found = -1;
@@ -309,14 +350,7 @@ __global__ void k_reverse(NbrArgs A) {
       if (A.seg) {
         const DevCfg& C = A.cfg[A.atom_cfg[i]];
         const int n_scan = (2 * C.kb[0] + 1) * (2 * C.kb[1] + 1) * (2 * C.kb[2] + 1);
-        const uint16_t* si = A.seg + i * kSegStride;
-        const int rel = static_cast<int>(p - A.off[i]);
-        int lo = 0, hi = n_scan - 1;   // the last q with si[q] <= rel
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (si[mid] <= rel) lo = mid; else hi = mid - 1;
-        }
-        const int qm = n_scan - 1 - lo;
+        const int qm = n_scan - 1 - min(static_cast<int>(A.pq[p]), n_scan - 1);
         const uint16_t* sj = A.seg + static_cast<long long>(j) * kSegStride;
         const long long oj1 = A.off[j + 1];
         const long long e1 = min(oj + sj[qm + 1], oj1);
@@ -408,6 +442,10 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
           slo.push_back(make_float4(ll[0], ll[1], ll[2], 0.f));
         }
     C.rc2 = rc * rc;
+    C.rcf = static_cast<float>(rc);
+    C.smax = 0.f;
+    for (size_t q = static_cast<size_t>(C.shift_base); q < shi.size(); ++q)
+      C.smax = std::max(C.smax, std::max(std::fabs(shi[q].x), std::max(std::fabs(shi[q].y), std::fabs(shi[q].z))));
     C.rc2f = static_cast<float>(rc * rc);
     C.rcm2f = static_cast<float>((rc + 1e-3) * (rc + 1e-3));
     for (int64_t a0 = ao[k]; a0 < ao[k + 1]; a0 += 4096) {
@@ -426,6 +464,8 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   DevCfg* d_cfg = nb->plan.as<DevCfg>();
   float4* d_shi = reinterpret_cast<float4*>(reinterpret_cast<char*>(d_cfg) + ((cfgs.size() * sizeof(DevCfg) + 15) & ~size_t(15)));
   float4* d_slo = d_shi + shi.size();
+  unsigned* d_xmax = reinterpret_cast<unsigned*>(d_slo + slo.size());   // within the 64 spare bytes
+  MTP_CUDA(cudaMemsetAsync(d_xmax, 0, sizeof(unsigned), s));
   MTP_CUDA(cudaMemcpyAsync(d_cfg, cfgs.data(), cfgs.size() * sizeof(DevCfg), cudaMemcpyHostToDevice, s));
   MTP_CUDA(cudaMemcpyAsync(d_shi, shi.data(), shi.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
   MTP_CUDA(cudaMemcpyAsync(d_slo, slo.data(), slo.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
@@ -478,6 +518,7 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.cnt = nb->counts.as<long long>();
   A.off = nb->off.as<long long>();
   A.err = m->err_flag.as<unsigned>();
+  A.xmax = d_xmax;
   nb->masks.ensure(static_cast<size_t>(N) * kMaskWords * sizeof(uint32_t), s);
   A.mask = nb->masks.as<uint32_t>();
   const int TB = 256;
@@ -527,8 +568,9 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
     // the hints are 16-bit offsets into an atom's list; the search clamps them to the list, so a
     // list longer than 65535 pairs only loses the hint (the whole list is searched)
     if (max_scan < kSegStride) {
-      nb->segs.ensure(static_cast<size_t>(std::max<int64_t>(N, 1)) * kSegStride * sizeof(uint16_t), s);
+      nb->segs.ensure(static_cast<size_t>(std::max<int64_t>(N, 1)) * kSegStride * sizeof(uint16_t) + P + 16, s);
       A.seg = nb->segs.as<uint16_t>();
+      A.pq = reinterpret_cast<uint8_t*>(A.seg + static_cast<size_t>(std::max<int64_t>(N, 1)) * kSegStride);
     }
   }
   // fill (at the counted offsets) and reverse pairs; a fill that disagrees with its count sets

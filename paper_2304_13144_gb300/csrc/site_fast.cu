@@ -130,6 +130,11 @@ struct FastParams {
   SiteOutputs o;
   int NQ, CBN, NC, NV;  // NV: per-neighborhood value slots, padded to a multiple of 4
   bool row_stage;       // rows are assembled in the adjoint buffer and written as float4
+  // aux_off > 0: the pair-adjoint scratch (dV/df per pair, Q per pair, species per pair, the
+  // radial block of b_i) lives in the adjoint array of the neighborhood being finished, from slot
+  // aux_off on: after the contraction only the adjoints of the moments (slots below the moment
+  // count) are read again, so the rest of the array is free
+  int aux_off;
   size_t c_bytes, tab_bytes, sched_bytes, warp_bytes, total;
   // word offsets of the schedule arrays inside the shared-memory copy
   int o_fslab, o_fround, o_frdst, o_rslab, o_rround, o_rrval, o_seed;
@@ -307,24 +312,18 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
   gradsA[1] = valsA[1] + NV;
   // padding terms read vals[0] and grads[0]: keep every entry finite from the start
   for (int k = lane; k < 4 * NV; k += 32) valsA[0][k] = 0.f;
-  float* GMb = gradsA[1] + NV;      // 32 x NR
-  float* PQb = GMb + 32 * NR;       // 32 x NQ
-  float* CBA[2];
-  CBA[0] = PQb + 32 * NQ;           // CBN each
-  CBA[1] = CBA[0] + CBN;
-  int* ZJ = reinterpret_cast<int*>(CBA[1] + CBN);
+  // pair-adjoint scratch: [GM 32 x NR | PQ 32 x NQ | ZJ 32 | CB], per warp or per adjoint array
+  float* const aux_warp = gradsA[1] + NV;
   __syncthreads();
   const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
 
   // ---------------- moments of one neighborhood (eq. 3) ----------------
-  auto moments = [&](int64_t i, float* vals, float* CB) {
+  auto moments = [&](int64_t i, float* vals) {
     const int zi = P.type[i];
     const int64_t p0 = P.nb.off[i];
     const int np = static_cast<int>(P.nb.off[i + 1] - p0);
     const float* czi = ctab + static_cast<size_t>(zi) * T * NR * NQ;
     for (int c = lane; c < Sh::NCOMP; c += 32) vals[c] = 0.f;
-    if (MODE & F_ROWS)
-      for (int e = lane; e < CBN; e += 32) CB[e] = 0.f;
     __syncwarp();
     for (int base = 0; base < np; base += 32) {
       const bool act = base + lane < np;
@@ -347,7 +346,16 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
   };
 
   // ---------------- pair adjoint and outputs of one neighborhood ----------------
-  auto finish = [&](int64_t wk, int64_t i, const float* vals, const float* grads, float* CB) {
+  auto finish = [&](int64_t wk, int64_t i, const float* vals, const float* grads) {
+    float* const aux = P.aux_off > 0 ? const_cast<float*>(grads) + P.aux_off : aux_warp;
+    float* const GMb = aux;                 // 32 x NR
+    float* const PQb = GMb + 32 * NR;       // 32 x NQ
+    int* const ZJ = reinterpret_cast<int*>(PQb + 32 * NQ);
+    float* const CB = PQb + 32 * NQ + 32;   // CBN
+    if (MODE & F_ROWS) {
+      for (int e = lane; e < CBN; e += 32) CB[e] = 0.f;
+      __syncwarp();
+    }
     const int zi = P.type[i];
     const int64_t p0 = P.nb.off[i];
     const int np = static_cast<int>(P.nb.off[i + 1] - p0);
@@ -489,8 +497,8 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
     const bool two = wk1 < P.n_work;
     const int64_t i0 = P.o.atom_list ? P.o.atom_list[wk0] : wk0;
     const int64_t i1 = two ? (P.o.atom_list ? P.o.atom_list[wk1] : wk1) : i0;
-    moments(i0, valsA[0], CBA[0]);
-    if (two) moments(i1, valsA[1], CBA[1]);
+    moments(i0, valsA[0]);
+    if (two) moments(i1, valsA[1]);
     float* v0 = valsA[0];
     float* v1 = valsA[1];
     float* g0 = gradsA[0];
@@ -510,8 +518,16 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         }
       };
       // ---------------- forward contraction (eqs. 5-6): both neighborhoods per term ----------------
+      // round headers are read one round ahead (the schedule copy is never written)
+      int4 rd_n = d.n_fround > 0 ? s_fround[0] : make_int4(0, 0, 0, 0);
+      int dst_n = d.n_fround > 0 ? s_frdst[lane] : -1;
       for (int r = 0; r < d.n_fround; ++r) {
-        const int4 rd = s_fround[r];
+        const int4 rd = rd_n;
+        const int dst = dst_n;
+        if (r + 1 < d.n_fround) {
+          rd_n = s_fround[r + 1];
+          dst_n = s_frdst[32 * (r + 1) + lane];
+        }
         const uint32_t* slab = s_fslab + rd.y + lane;
         float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
         int it = 0;
@@ -535,7 +551,6 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
           a0 = fmaf(c0, v0[x0] * v0[y0], a0);
           b0 = fmaf(c0, v1[x0] * v1[y0], b0);
         }
-        const int dst = s_frdst[32 * r + lane];
         if (dst >= 0) {
           v0[dst] = a0 + a1;
           v1[dst] = b0 + b1;
@@ -543,11 +558,21 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         if (rd.z) __syncwarp();
       }
       // ---------------- adjoint of the contraction (gather form): both neighborhoods ----------------
+      rd_n = d.n_rround > 0 ? s_rround[0] : make_int4(0, 0, 0, 0);   // the adjoint's headers likewise
+      int x_n = d.n_rround > 0 ? s_rrval[lane] : -1;
+      float sd_n = x_n >= 0 ? s_seed[x_n] : 0.f;
+      int x_nn = d.n_rround > 1 ? s_rrval[32 + lane] : -1;
       for (int r = 0; r < d.n_rround; ++r) {
-        const int4 rd = s_rround[r];
+        const int4 rd = rd_n;
+        const int x = x_n;
+        const float sd = sd_n;
+        if (r + 1 < d.n_rround) {
+          rd_n = s_rround[r + 1];
+          x_n = x_nn;
+          sd_n = x_n >= 0 ? s_seed[x_n] : 0.f;
+        }
+        if (r + 2 < d.n_rround) x_nn = s_rrval[32 * (r + 2) + lane];
         const uint32_t* slab = s_rslab + rd.y + lane;
-        const int x = s_rrval[32 * r + lane];
-        const float sd = x >= 0 ? s_seed[x] : 0.f;
         float a0 = sd, a1 = 0.f, b0 = sd, b1 = 0.f;
         int it = 0;
         for (; it + 2 <= rd.x; it += 2) {
@@ -578,8 +603,8 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
     };
     if (d.coef_inline) contract(std::true_type{});
     else contract(std::false_type{});
-    finish(wk0, i0, v0, g0, CBA[0]);
-    if (two) finish(wk1, i1, v1, g1, CBA[1]);
+    finish(wk0, i0, v0, g0);
+    if (two) finish(wk1, i1, v1, g1);
   }
 }
 
@@ -631,8 +656,15 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   P.row_stage = o.rows_ld > 0 && o.rows_ld <= d.n_vals && (o.rows_ld & 3) == 0;
   P.c_bytes = (static_cast<size_t>(P.NC) * sizeof(float) + 15) & ~size_t(15);
   P.tab_bytes = ((256 + d.n_mom) * sizeof(float) + 15) & ~size_t(15);
-  P.warp_bytes = ((4 * static_cast<size_t>(P.NV) + 32 * (d.n_rad + d.n_q) + 2 * P.CBN) * sizeof(float) +
-                  32 * sizeof(int) + 15) & ~size_t(15);
+  // pair-adjoint scratch inside the finished neighborhood's adjoint array when it fits above the
+  // moment adjoints, with its radial block at or above the staged row (which rewrites [0, ld))
+  // and below the zero slot n_vals; otherwise one scratch block per warp
+  const int aux_head = 32 * (d.n_rad + d.n_q) + 32;   // GM, PQ, ZJ before the radial block
+  const int aux_need = aux_head + P.CBN;
+  int aux_off = std::max((d.n_mom + 3) & ~3, (P.row_stage ? static_cast<int>(o.rows_ld) : 0) - aux_head);
+  aux_off = (aux_off + 3) & ~3;
+  P.aux_off = (rows && aux_off + aux_need <= d.n_vals) ? aux_off : 0;
+  P.warp_bytes = ((4 * static_cast<size_t>(P.NV) + (P.aux_off > 0 ? 0 : aux_need)) * sizeof(float) + 15) & ~size_t(15);
   // shared-memory copy of the schedule (32-bit words); fwd_global: without the forward slab
   const int nu0 = d.nu_max, nr = d.n_rad;
   const bool fg_shape = nr == 5 && nu0 == 8;   // the shape with a global-forward instantiation
@@ -661,7 +693,10 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   if (!fg && ws == 0) return false;
   P = fg ? Pg : Ps;
   int nwarps = fg ? wg : ws;
+  // untuned default: at most 7 warps with the forward schedule in global memory (with 8 the
+  // shared-memory carve-out leaves the forward schedule less L1 and the kernel runs slower)
   if (m->tune_warps_fast > 0) nwarps = std::min(nwarps, m->tune_warps_fast);
+  else if (fg) nwarps = std::min(nwarps, 7);
   m->last_warps = nwarps;
   m->last_fast = true;
   m->last_fwd_global = fg;
