@@ -30,8 +30,6 @@ struct DevCfg {
   long long bin_base, shift_base;
   float rc2f, rcm2f;
   double rc2;
-  float rcf;    // R_cut in FP32
-  float smax;   // largest |component| of the configuration's image shifts (FP32 high parts)
 };
 
 struct NbrArgs {
@@ -67,7 +65,6 @@ struct NbrArgs {
   uint32_t* mask;        // [kMaskWords x n_atoms] accepted bits of the first kMaskBits candidates
                          // in scan order, by bin-order position (count pass writes, fill reads)
   unsigned* err;
-  unsigned* xmax;        // bits of the largest |component| of any wrapped position (FP32 high parts)
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -116,12 +113,7 @@ __global__ void k_prep(NbrArgs A) {
   float h[3], l[3];
   for (int c = 0; c < 3; ++c) { h[c] = __double2float_rn(xw[c]); l[c] = __double2float_rn(xw[c] - static_cast<double>(h[c])); }
   A.ph[i] = make_float4(h[0], h[1], h[2], __int_as_float(static_cast<int>(i)));
-  {
-    // non-negative floats order like their bit patterns: one atomic per warp
-    const unsigned hb = __float_as_uint(fmaxf(fabsf(h[0]), fmaxf(fabsf(h[1]), fabsf(h[2]))));
-    const unsigned wm = __reduce_max_sync(__activemask(), hb);
-    if (hb == wm) atomicMax(A.xmax, wm);
-  }
+
   A.pl[i] = make_float4(l[0], l[1], l[2], __int_as_float(wpk));   // .w: the packed wrap
   long long bin = C.bin_base + (static_cast<long long>(b[0]) * C.nb[1] + b[1]) * C.nb[2] + b[2];
   A.atom_bin[i] = bin;
@@ -220,18 +212,6 @@ __global__ void k_pairs(NbrArgs A) {
   long long out = FILL ? A.off[i] : 0;
   const long long out_end = FILL ? A.off[i + 1] : 0;
   long long count = 0;
-  // count pass: a candidate whose FP32 estimate |a|, a = (x_j - x_i) + shift (high parts), is
-  // below t_fast is a pair without forming r_ij.  |a - r_ij| <= b per component with
-  // b = 2^-24 (4 X + 2 S + R_cut) (X, S: largest wrapped-position and shift components), so
-  // |a|^2 < (R_cut (1 - 1e-5) - 2 b)^2 puts r_ij^2 below R_cut^2 (1 - 1.6e-5): outside the
-  // band that decide() settles in FP64, on the accepting side.  |a|^2 > 1e-6 keeps coincident
-  // atoms on the full path.
-  float t_fast = 0.f;
-  if (!FILL) {
-    const float b = 5.9604645e-8f * 1.1f * (4.f * __uint_as_float(*A.xmax) + 2.f * C.smax + C.rcf);
-    const float rr = C.rcf * (1.f - 1e-5f) - 2.f * b;
-    if (b < 1e-4f && rr > 0.f) t_fast = rr * rr;
-  }
   int cand = 0;          // candidate index in scan order (the self candidate included)
   uint32_t mword = 0;    // count pass: accepted bits of the current mask word
   // segment starts: bins are scanned in increasing q = ((d0 + kb0) w1 + (d1 + kb1)) w2 + (d2 + kb2);
@@ -263,18 +243,11 @@ __global__ void k_pairs(NbrArgs A) {
           for (; q_next <= q; ++q_next) seg[q_next] = static_cast<uint16_t>(count);
         const long long tb = C.bin_base + (static_cast<long long>(t0) * C.nb[1] + t1) * C.nb[2] + t2;
         const long long s0 = A.bin_start[tb], s1 = A.bin_start[tb + 1];
-        const float4 sh_b = A.sh_hi[C.shift_base + ((static_cast<long long>(n0 + C.K) * (2 * C.K + 1) + (n1 + C.K)) * (2 * C.K + 1) + (n2 + C.K))];
         // candidate s of this bin: 1 if (i -> j, n) is a pair (written out in the fill pass)
         auto test = [&](long long s) -> int {
           const float4 xj_h = A.bph[s];
           const int j = __float_as_int(xj_h.w);
           if (j == static_cast<int>(i) && n0 == 0 && n1 == 0 && n2 == 0) return 0;
-          if (!FILL) {
-            const float ax = (xj_h.x - xi_h.x) + sh_b.x, ay = (xj_h.y - xi_h.y) + sh_b.y, az = (xj_h.z - xi_h.z) + sh_b.z;
-            const float q = ax * ax + ay * ay + az * az;
-            if (q > C.rcm2f) return 0;
-            if (q < t_fast && q > 1e-6f) { ++count; return 1; }
-          }
           float4 r;
           int img;
           if (!decide(A, C, i, j, xi_h, xi_l, xj_h, A.bpl[s], n0, n1, n2, r, img)) return 0;
@@ -324,6 +297,158 @@ __global__ void k_pairs(NbrArgs A) {
     A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + t] = mword;
   if (!FILL) A.cnt[i] = count;
   else if (count != out_end - A.off[i]) atomicOr(A.err, ERRF_CAPACITY);
+}
+
+// Fill pass with one warp per atom (bin order), for configurations that scan at most 27 bins:
+// lane q owns scanned bin q (its first binned atom, size, image and first candidate index), the
+// count pass's accepted bits are located by prefix popcounts, and lane k forms the atom's k-th
+// pair, so consecutive lanes write consecutive slots.  Candidates past the recorded bits are
+// decided again, 32 at a time, and compacted by ballot.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int rem) {   // position of set bit #rem (0-based)
+  int pos = 0;
+#pragma unroll
+  for (int width = 16; width; width >>= 1) {
+    const int low = __popc(m & ((1u << width) - 1u));
+    if (rem >= low) { rem -= low; m >>= width; pos += width; }
+  }
+  return pos;
+}
+
+__global__ void __launch_bounds__(256) k_fill_warp(NbrArgs A) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t t = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  if (t >= A.n_atoms) return;   // whole warps leave together
+  const int64_t i = A.bin_atoms[t];
+  const DevCfg& C = A.cfg[A.atom_cfg[i]];
+  const long long bin = A.atom_bin[i] - C.bin_base;
+  const int b[3] = {static_cast<int>(bin / (static_cast<long long>(C.nb[1]) * C.nb[2])),
+                    static_cast<int>((bin / C.nb[2]) % C.nb[1]), static_cast<int>(bin % C.nb[2])};
+  const float4 xi_h = A.ph[i], xi_l = A.pl[i];
+  const long long out0 = A.off[i], out1 = A.off[i + 1];
+  const int w1 = 2 * C.kb[1] + 1, w2 = 2 * C.kb[2] + 1;
+  const int n_scan = (2 * C.kb[0] + 1) * w1 * w2;
+  // scanned bin of this lane (same order as k_pairs): first binned atom, size, image
+  int n[3] = {0, 0, 0};
+  long long s0 = 0;
+  int sz = 0;
+  if (lane < n_scan) {
+    const int d[3] = {lane / (w1 * w2) - C.kb[0], (lane / w2) % w1 - C.kb[1], lane % w2 - C.kb[2]};
+    int tt[3];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      tt[a] = b[a] + d[a];
+      if (C.pbc[a]) {
+        if (tt[a] < 0 || tt[a] >= C.nb[a]) {
+          n[a] = (tt[a] >= 0) ? tt[a] / C.nb[a] : -((-tt[a] + C.nb[a] - 1) / C.nb[a]);
+          tt[a] -= n[a] * C.nb[a];
+        }
+      } else if (tt[a] < 0 || tt[a] >= C.nb[a]) {
+        ok = false;
+      }
+    }
+    if (ok) {
+      const long long tb = C.bin_base + (static_cast<long long>(tt[0]) * C.nb[1] + tt[1]) * C.nb[2] + tt[2];
+      s0 = A.bin_start[tb];
+      sz = static_cast<int>(A.bin_start[tb + 1] - s0);
+    }
+  }
+  // first candidate index of each scanned bin (exclusive prefix of the sizes)
+  int cst0 = sz;
+  for (int m = 1; m < 32; m <<= 1) {
+    const int v = __shfl_up_sync(full, cst0, m);
+    if (lane >= m) cst0 += v;
+  }
+  const int ctot = __shfl_sync(full, cst0, 31);
+  cst0 -= sz;
+  const int cst = lane < n_scan ? cst0 : 0x7fffffff;   // lanes past the scan never match
+  auto bin_of = [&](int c) {   // the scanned bin holding candidate c: the last lane with cst <= c
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__shfl_sync(full, cst, mid) <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  // the count pass's bits of the first min(ctot, kMaskBits) candidates, one word per lane
+  const int nbits = min(ctot, kMaskBits);
+  uint32_t word = 0;
+  if (lane < kMaskWords && 32 * lane < nbits) {
+    word = A.mask[static_cast<long long>(lane) * A.n_atoms + t];
+    const int valid = nbits - 32 * lane;
+    if (valid < 32) word &= (1u << valid) - 1u;
+  }
+  int wpre = __popc(word);
+  for (int m = 1; m < 32; m <<= 1) {
+    const int v = __shfl_up_sync(full, wpre, m);
+    if (lane >= m) wpre += v;
+  }
+  const int nmask = __shfl_sync(full, wpre, 31);
+  wpre -= __popc(word);
+  // decide candidate c of scanned bin q again (every lane takes part in the shuffles)
+  auto form = [&](int c, int q, bool act, int& j, int& img, float4& r) -> int {
+    const long long sb = __shfl_sync(full, s0, q);
+    const int cq = __shfl_sync(full, cst0, q);
+    const int n0 = __shfl_sync(full, n[0], q), n1 = __shfl_sync(full, n[1], q), n2 = __shfl_sync(full, n[2], q);
+    if (!act) return 0;
+    const long long sidx = sb + (c - cq);
+    const float4 xj_h = A.bph[sidx];
+    j = __float_as_int(xj_h.w);
+    if (j == static_cast<int>(i) && n0 == 0 && n1 == 0 && n2 == 0) return 0;
+    return decide(A, C, i, j, xi_h, xi_l, xj_h, A.bpl[sidx], n0, n1, n2, r, img);
+  };
+  auto put = [&](long long o, int j, int img, const float4& r, int q) {
+    if (o >= out1) return;
+    A.pj[o] = j;
+    A.pimg[o] = img;
+    A.pr32[o] = r;
+    if (A.pq) A.pq[o] = static_cast<uint8_t>(q);
+  };
+  // accepted candidates among the recorded bits: lane k forms the atom's k-th pair
+  for (int kb = 0; kb < nmask; kb += 32) {
+    const int k = kb + lane;
+    const bool act = k < nmask;
+    int lo = 0, hi = kMaskWords - 1;   // the last word whose prefix count is <= k
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__shfl_sync(full, wpre, mid) <= k) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t ww = __shfl_sync(full, word, lo);
+    const int wp = __shfl_sync(full, wpre, lo);
+    const int c = act ? 32 * lo + nth_set_bit(ww, k - wp) : 0;
+    const int q = bin_of(c);
+    int j = 0, img = 0;
+    float4 r;
+    if (form(c, q, act, j, img, r)) put(out0 + k, j, img, r, q);
+    else if (act) atomicOr(A.err, ERRF_CAPACITY);   // the replay disagrees with the count
+  }
+  long long written = nmask;
+  // pairs before each scanned bin (segment starts): the recorded part ...
+  const int cseg = lane < n_scan ? cst0 : ctot;   // lane n_scan: the end of the list
+  int seg_v;
+  {
+    const int cm = min(cseg, nbits);
+    const int w = min(cm >> 5, 31);
+    const int wp = __shfl_sync(full, wpre, w);
+    const uint32_t ww = __shfl_sync(full, word, w);
+    seg_v = (cm >> 5) >= kMaskWords ? nmask : wp + __popc(ww & ((1u << (cm & 31)) - 1u));
+  }
+  // ... and candidates past the recorded bits, decided again and compacted in scan order
+  for (int cb = kMaskBits; cb < ctot; cb += 32) {
+    const int c = cb + lane;
+    const bool act = c < ctot;
+    const int q = bin_of(act ? c : cb);
+    int j = 0, img = 0;
+    float4 r;
+    const int acc = form(c, q, act, j, img, r);
+    const unsigned bal = __ballot_sync(full, acc != 0);
+    if (acc) put(out0 + written + __popc(bal & ((1u << lane) - 1u)), j, img, r, q);
+    const int lim = cseg - cb;   // this round's candidates before the lane's segment start
+    if (lim > 0) seg_v += __popc(bal & (lim >= 32 ? full : ((1u << lim) - 1u)));
+    written += __popc(bal);
+  }
+  if (A.seg && lane <= n_scan) A.seg[i * kSegStride + lane] = static_cast<uint16_t>(seg_v);
+  if (lane == 0 && written != out1 - out0) atomicOr(A.err, ERRF_CAPACITY);
 }
 
 // prev[p] = index of the reverse pair (j -> i, -image) of pair p = (i -> j, image): one warp
@@ -442,10 +567,6 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
           slo.push_back(make_float4(ll[0], ll[1], ll[2], 0.f));
         }
     C.rc2 = rc * rc;
-    C.rcf = static_cast<float>(rc);
-    C.smax = 0.f;
-    for (size_t q = static_cast<size_t>(C.shift_base); q < shi.size(); ++q)
-      C.smax = std::max(C.smax, std::max(std::fabs(shi[q].x), std::max(std::fabs(shi[q].y), std::fabs(shi[q].z))));
     C.rc2f = static_cast<float>(rc * rc);
     C.rcm2f = static_cast<float>((rc + 1e-3) * (rc + 1e-3));
     for (int64_t a0 = ao[k]; a0 < ao[k + 1]; a0 += 4096) {
@@ -464,8 +585,6 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   DevCfg* d_cfg = nb->plan.as<DevCfg>();
   float4* d_shi = reinterpret_cast<float4*>(reinterpret_cast<char*>(d_cfg) + ((cfgs.size() * sizeof(DevCfg) + 15) & ~size_t(15)));
   float4* d_slo = d_shi + shi.size();
-  unsigned* d_xmax = reinterpret_cast<unsigned*>(d_slo + slo.size());   // within the 64 spare bytes
-  MTP_CUDA(cudaMemsetAsync(d_xmax, 0, sizeof(unsigned), s));
   MTP_CUDA(cudaMemcpyAsync(d_cfg, cfgs.data(), cfgs.size() * sizeof(DevCfg), cudaMemcpyHostToDevice, s));
   MTP_CUDA(cudaMemcpyAsync(d_shi, shi.data(), shi.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
   MTP_CUDA(cudaMemcpyAsync(d_slo, slo.data(), slo.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
@@ -518,7 +637,6 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.cnt = nb->counts.as<long long>();
   A.off = nb->off.as<long long>();
   A.err = m->err_flag.as<unsigned>();
-  A.xmax = d_xmax;
   nb->masks.ensure(static_cast<size_t>(N) * kMaskWords * sizeof(uint32_t), s);
   A.mask = nb->masks.as<uint32_t>();
   const int TB = 256;
@@ -576,14 +694,17 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   // fill (at the counted offsets) and reverse pairs; a fill that disagrees with its count sets
   // ERRF_CAPACITY: the pass is repeated once, then the build fails with MTP_ERR_CAPACITY
   for (int attempt = 0;; ++attempt) {
-    ProfRegion* pr2 = new ProfRegion("neighbors_fill_reverse", s);
-    k_pairs<true><<<blocks_for(N, 128), 128, 0, s>>>(A);
-    MTP_CUDA(cudaGetLastError());
+    {
+      ProfRegion pr2("neighbors_fill", s);
+      if (A.seg) k_fill_warp<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
+      else k_pairs<true><<<blocks_for(N, 128), 128, 0, s>>>(A);
+      MTP_CUDA(cudaGetLastError());
+    }
     if (total > 0) {
+      ProfRegion pr3("neighbors_reverse", s);
       k_reverse<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
       MTP_CUDA(cudaGetLastError());
     }
-    delete pr2;
     MTP_CUDA(cudaMemcpyAsync(&flag, m->err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     MTP_CUDA(cudaStreamSynchronize(s));
     if (take_injected(g_inject_overflow)) flag |= ERRF_CAPACITY;

@@ -9,8 +9,6 @@
 #include <thrust/iterator/counting_iterator.h>
 #include <cuda_runtime.h>
 
-#include <type_traits>
-
 #include <algorithm>
 
 #include "mtp_internal.h"
@@ -21,43 +19,67 @@ namespace {
 
 int nblk(int64_t n, int t) { return static_cast<int>(std::max<int64_t>(1, (n + t - 1) / t)); }
 
-template <class R>
-__global__ void k_forces(DevNbr nb, const R* G, double* F) {
+// FP64 gradients: one thread per atom, pairs in list order
+__global__ void k_forces(DevNbr nb, const double* G, double* F) {
   int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= nb.n_atoms) return;
-  if constexpr (std::is_same<R, float>::value) {
-    // FP32 gradients: each component summed as an unevaluated pair hi + lo of floats with
-    // error-free additions (TwoSum), so the sum is as accurate as an FP64 accumulation while
-    // running on the FP32 pipes (FP64 throughput is a small fraction of FP32 on this GPU)
-    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
-    auto add = [](float& hi, float& lo, float x) {
-      const float s = __fadd_rn(hi, x);
-      const float bb = __fsub_rn(s, hi);
-      const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-      hi = s;
-      lo = __fadd_rn(lo, err);
-    };
-    for (int64_t p = nb.off[i]; p < nb.off[i + 1]; ++p) {
+  double f0 = 0, f1 = 0, f2 = 0;
+  for (int64_t p = nb.off[i]; p < nb.off[i + 1]; ++p) {
+    const int64_t q = nb.prev[p];
+    f0 += G[3 * p + 0] - G[3 * q + 0];
+    f1 += G[3 * p + 1] - G[3 * q + 1];
+    f2 += G[3 * p + 2] - G[3 * q + 2];
+  }
+  F[3 * i + 0] = f0;
+  F[3 * i + 1] = f1;
+  F[3 * i + 2] = f2;
+}
+
+// FP32 gradients, LPA lanes per atom: each component summed as an unevaluated pair hi + lo of
+// floats with error-free additions (TwoSum), as accurate as an FP64 accumulation on the FP32
+// pipes (FP64 throughput is a small fraction of FP32 on this GPU); lane k of an atom's group
+// takes pairs k, k + LPA, ..., and the group combines its partial pairs in a fixed tree
+template <int LPA>
+__global__ void k_forces_grp(DevNbr nb, const float* G, double* F) {
+  const int64_t gid = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / LPA;
+  const int k = threadIdx.x & (LPA - 1);
+  const bool act = gid < nb.n_atoms;
+  const int64_t i = act ? gid : 0;
+  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+  auto two = [](float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  };
+  if (act) {
+    const int64_t p1 = nb.off[i + 1];
+    for (int64_t p = nb.off[i] + k; p < p1; p += LPA) {
       const int64_t q = nb.prev[p];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        add(h[c], l[c], G[3 * p + c]);
-        add(h[c], l[c], -G[3 * q + c]);
+        float s, e;
+        two(h[c], G[3 * p + c], s, e);
+        h[c] = s; l[c] = __fadd_rn(l[c], e);
+        two(h[c], -G[3 * q + c], s, e);
+        h[c] = s; l[c] = __fadd_rn(l[c], e);
       }
     }
+  }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) F[3 * i + c] = static_cast<double>(h[c]) + static_cast<double>(l[c]);
-  } else {
-    double f0 = 0, f1 = 0, f2 = 0;
-    for (int64_t p = nb.off[i]; p < nb.off[i + 1]; ++p) {
-      const int64_t q = nb.prev[p];
-      f0 += static_cast<double>(G[3 * p + 0]) - static_cast<double>(G[3 * q + 0]);
-      f1 += static_cast<double>(G[3 * p + 1]) - static_cast<double>(G[3 * q + 1]);
-      f2 += static_cast<double>(G[3 * p + 2]) - static_cast<double>(G[3 * q + 2]);
+  for (int m = LPA / 2; m; m >>= 1)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h[c], m), ol = __shfl_xor_sync(0xffffffffu, l[c], m);
+      // the lower lane of each pair adds the upper one's, so both get the same sum
+      float s, e;
+      if (k & m) two(oh, h[c], s, e); else two(h[c], oh, s, e);
+      h[c] = s;
+      l[c] = __fadd_rn(__fadd_rn((k & m) ? ol : l[c], (k & m) ? l[c] : ol), e);
     }
-    F[3 * i + 0] = f0;
-    F[3 * i + 1] = f1;
-    F[3 * i + 2] = f2;
+  if (act && k < 3) {
+    const float hv = k == 0 ? h[0] : (k == 1 ? h[1] : h[2]);
+    const float lv = k == 0 ? l[0] : (k == 1 ? l[1] : l[2]);
+    F[3 * i + k] = static_cast<double>(hv) + static_cast<double>(lv);
   }
 }
 
@@ -201,8 +223,8 @@ __global__ void k_sum_rows(const double* part, int nrows, int64_t m, double* out
 
 void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStream_t s) {
   ProfRegion pr("force_gather", s);
-  if (fp64) k_forces<double><<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const double*>(G), F);
-  else k_forces<float><<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const float*>(G), F);
+  if (fp64) k_forces<<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const double*>(G), F);
+  else k_forces_grp<8><<<nblk(nb->n_atoms * 8, 256), 256, 0, s>>>(nb->dn, static_cast<const float*>(G), F);
   MTP_CUDA(cudaGetLastError());
 }
 

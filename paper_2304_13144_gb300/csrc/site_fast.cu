@@ -400,9 +400,9 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         const float s = rad / rr;
         gx = fmaf(s, rx, gx); gy = fmaf(s, ry, gy); gz = fmaf(s, rz, gz);
         float* Gout = static_cast<float*>(P.o.G);
-        Gout[3 * p + 0] = gx;
-        Gout[3 * p + 1] = gy;
-        Gout[3 * p + 2] = gz;
+        __stcs(Gout + 3 * p + 0, gx);
+        __stcs(Gout + 3 * p + 1, gy);
+        __stcs(Gout + 3 * p + 2, gz);
         const float g3[3] = {gx, gy, gz}, r3[3] = {rx, ry, rz};
 #pragma unroll
         for (int a2 = 0; a2 < 3; ++a2)
@@ -480,8 +480,8 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
           const float4 v = src[k];
           if (lo) {
             const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
-            hi[k] = h;
-            lo[k] = make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+            __stcs(hi + k, h);
+            __stcs(lo + k, make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w)));
           } else {
             hi[k] = v;
           }
@@ -693,8 +693,8 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   if (!fg && ws == 0) return false;
   P = fg ? Pg : Ps;
   int nwarps = fg ? wg : ws;
-  // untuned default: at most 7 warps with the forward schedule in global memory (with 8 the
-  // shared-memory carve-out leaves the forward schedule less L1 and the kernel runs slower)
+  // untuned default: at most 7 warps with the forward schedule in global memory (8 fit at level
+  // 20 but ran 5 % slower there); mtp_autotune times every shape
   if (m->tune_warps_fast > 0) nwarps = std::min(nwarps, m->tune_warps_fast);
   else if (fg) nwarps = std::min(nwarps, 7);
   m->last_warps = nwarps;
