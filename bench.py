@@ -421,7 +421,9 @@ def run_ours(args):
                    "n_atoms": N, "n_pairs": n_pairs, "precision": "mixed (FP32 compute, FP64 sums)",
                    "l2": "inputs larger than L2 (pair list and parameter rows exceed 129 MB)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU",
-                   "autotuned_warps_per_block": {p: w for p, (w, _) in tuned.items()}},
+                   "autotuned_warps_per_block": {p: w for p, (w, _) in tuned.items()},
+                   "launch_shape": dict(zip(("warps_mixed_kernel", "forward_schedule_in_global", "warps_generic_kernel"),
+                                            api.mtp_get_launch_shape(model)))},
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms_fp64 / args.fp64_steps,
                       "steps": args.fp64_steps, "mixed_over_fp64": value / fp64_value},
         "errors_mixed_vs_fp64": {"max_abs_dF_eV_per_A": dF, "abs_dE_per_atom_eV": dE, "rel_dW": dW,

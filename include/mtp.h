@@ -293,6 +293,13 @@ mtp_status mtp_fit_bfgs(mtp_model* model, const mtp_batch* batch, const mtp_nbr*
 mtp_status mtp_autotune(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
                         mtp_precision prec, int32_t* warps, double* ms, void* stream);
 
+/* The launch shapes the autotuner left in the model (HOST outputs, any may be NULL):
+ * warps_fast = warps per block of the specialised mixed kernel (0: untuned, the default shape),
+ * fwd_global = forward contraction schedule in global (1) or shared (0) memory (-1: untuned),
+ * warps_generic = warps per block of the generic kernel (0: untuned).  No GPU work. */
+mtp_status mtp_get_launch_shape(const mtp_model* model, int32_t* warps_fast, int32_t* fwd_global,
+                                int32_t* warps_generic);
+
 /* Checkpoint (the paper keeps theta, the active set and its mode in its .almtp file): the
  * model's descriptor, theta and, if loaded, the active-set matrix A, in a HOST byte buffer
  * (magic "MTP1", version 1, then mtp_desc, m, theta[m] FP64, a flag and A[m x m] FP64, native

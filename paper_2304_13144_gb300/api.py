@@ -473,6 +473,13 @@ def mtp_autotune(model, batch, nbr, prec="mixed", stream=None):
     return w.value, ms.value
 
 
+def mtp_get_launch_shape(model):
+    """The autotuner's shapes kept in the model: (warps_fast, fwd_global, warps_generic)."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().mtp_get_launch_shape(model.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
 def mtp_save(model, stream=None) -> bytes:
     """Checkpoint of the model (descriptor, theta, active set) as bytes."""
     size = ctypes.c_int64()

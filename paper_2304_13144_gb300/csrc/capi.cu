@@ -627,10 +627,19 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     double* gamma = md->have_ainv ? gam : nullptr;
     // the pass that mtp_step makes (energies, forces, virial and, with an active set, the grade)
     auto run = [&] { efs_and_grade(md, b, nb, prec, E, nullptr, F, W, 0.0, gamma, nullptr, nullptr, nullptr, s); };
+    // the first pass (default shape) shows which kernel this precision runs; the other kernel's
+    // tuned shape is kept
+    const int keep_fast = md->tune_warps_fast, keep_fwd = md->tune_fwd_global, keep_gen = md->tune_warps_generic;
     md->tune_warps_fast = md->tune_warps_generic = 0;
     md->tune_fwd_global = -1;
     run();
     const bool fast = md->last_fast;
+    if (fast) {
+      md->tune_warps_generic = keep_gen;
+    } else {
+      md->tune_warps_fast = keep_fast;
+      md->tune_fwd_global = keep_fwd;
+    }
     int& knob = fast ? md->tune_warps_fast : md->tune_warps_generic;
     const int max_w = fast ? 8 : 4;
     cudaEvent_t e0, e1;
@@ -668,6 +677,16 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     MTP_CUDA(cudaStreamSynchronize(s));
     if (warps) *warps = best_w;
     if (ms) *ms = best_ms;
+  });
+}
+
+mtp_status mtp_get_launch_shape(const mtp_model* md, int32_t* warps_fast, int32_t* fwd_global,
+                                int32_t* warps_generic) {
+  return guarded([&] {
+    if (!md) throw Fail{MTP_ERR_ARG, "null model"};
+    if (warps_fast) *warps_fast = md->tune_warps_fast;
+    if (fwd_global) *fwd_global = md->tune_fwd_global;
+    if (warps_generic) *warps_generic = md->tune_warps_generic;
   });
 }
 

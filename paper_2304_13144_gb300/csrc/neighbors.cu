@@ -314,7 +314,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int rem) {   // position 
   return pos;
 }
 
-__global__ void __launch_bounds__(256) k_fill_warp(NbrArgs A) {
+__global__ void __launch_bounds__(256, 4) k_fill_warp(NbrArgs A) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t t = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;

@@ -687,8 +687,10 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   FastParams Ps = P, Pg = P;
   const int ws = layout(false, Ps);
   const int wg = fg_shape ? layout(true, Pg) : 0;
-  // placement: the tuned one, else the one with more warps per SM (shared memory on ties)
-  bool fg = m->tune_fwd_global >= 0 ? (m->tune_fwd_global == 1 && wg > 0) : (wg > ws);
+  // placement: the tuned one, else the one with more warps per SM once the global-forward
+  // placement's default cap of 7 is applied (shared memory on ties: measured faster, the forward
+  // slab then does not compete for L1)
+  bool fg = m->tune_fwd_global >= 0 ? (m->tune_fwd_global == 1 && wg > 0) : (std::min(wg, 7) > ws);
   if (!fg && ws == 0) fg = wg > 0;
   if (!fg && ws == 0) return false;
   P = fg ? Pg : Ps;

@@ -35,3 +35,22 @@ def test_autotune_keeps_results(api, lev, prec):
     after = api.mtp_step(model, b, nb, prec)
     for k, v in before.items():
         assert torch.equal(after[k], v), k
+
+
+def test_autotune_of_one_precision_keeps_the_other(api):
+    """Tuning the FP64 (generic) kernel after the mixed one leaves the mixed shape in place."""
+    md = O.OracleModel(3, 20, 2.0, 5.0)
+    nu_sum = [sum(nu for _, nu in labs) for labs, _ in md.basis]
+    nf = [len(labs) for labs, _ in md.basis]
+    theta = synth.draw_theta(104, 3, md.n_rad, md.n_q, nu_sum, nf, 2.0, 5.0, 42.0)
+    model = api.mtp_load(api.make_desc(3, 20), theta)
+    b = api.Batch(synth.fcc_ternary(seed=105, n=10))
+    nb = api.mtp_build_neighbors(model, b)
+    assert api.mtp_get_launch_shape(model) == (0, -1, 0)
+    w_mixed, _ = api.mtp_autotune(model, b, nb, "mixed")
+    fast, fwd, gen = api.mtp_get_launch_shape(model)
+    assert fast == w_mixed and fwd in (0, 1) and gen == 0
+    w_fp64, _ = api.mtp_autotune(model, b, nb, "fp64")
+    assert api.mtp_get_launch_shape(model) == (fast, fwd, w_fp64)
+    api.mtp_autotune(model, b, nb, "mixed")
+    assert api.mtp_get_launch_shape(model)[2] == w_fp64
