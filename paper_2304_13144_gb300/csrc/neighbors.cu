@@ -30,6 +30,7 @@ struct DevCfg {
   long long bin_base, shift_base;
   float rc2f, rcm2f;
   double rc2;
+  int qd[32];   // scanned bin q -> packed offsets (d0 + 64) | (d1 + 64) << 8 | (d2 + 64) << 16
 };
 
 struct NbrArgs {
@@ -45,6 +46,7 @@ struct NbrArgs {
   int* atom_cfg;
   int* wrap;             // packed integer wrap of each atom
   long long* atom_bin;   // global bin of each atom
+  int* bcoord;           // the atom's bin coordinates within its configuration, 10 bits each
   float4* ph;            // wrapped position hi (.w = atom index bits)
   float4* pl;            // wrapped position lo (.w = packed wrap of the atom)
   int* bin_count;
@@ -117,6 +119,7 @@ __global__ void k_prep(NbrArgs A) {
   A.pl[i] = make_float4(l[0], l[1], l[2], __int_as_float(wpk));   // .w: the packed wrap
   long long bin = C.bin_base + (static_cast<long long>(b[0]) * C.nb[1] + b[1]) * C.nb[2] + b[2];
   A.atom_bin[i] = bin;
+  A.bcoord[i] = b[0] | (b[1] << 10) | (b[2] << 20);
   atomicAdd(&A.bin_count[bin], 1);
 }
 
@@ -196,18 +199,18 @@ constexpr int kSegStride = 28;   // segment starts per atom: up to 27 scanned bi
 constexpr int kMaskWords = 16;   // accepted-candidate bits per atom recorded by the count pass
 constexpr int kMaskBits = 32 * kMaskWords;
 
+// (at most 48 registers, 10 CTAs of 128 threads per SM: measured faster than 66 registers and
+// 7 CTAs despite a few spilled loop variables)
 template <bool FILL>
-__global__ void k_pairs(NbrArgs A) {
+__global__ void __launch_bounds__(128, 10) k_pairs(NbrArgs A) {
   // threads take the atoms in bin order, so that a warp's atoms scan the same or adjacent bins
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= A.n_atoms) return;
   const int64_t i = A.bin_atoms[t];
   const int k = A.atom_cfg[i];
   const DevCfg& C = A.cfg[k];
-  const long long bin = A.atom_bin[i] - C.bin_base;
-  const int b0 = static_cast<int>(bin / (static_cast<long long>(C.nb[1]) * C.nb[2]));
-  const int b1 = static_cast<int>((bin / C.nb[2]) % C.nb[1]);
-  const int b2 = static_cast<int>(bin % C.nb[2]);
+  const int bc = A.bcoord[i];
+  const int b0 = bc & 1023, b1 = (bc >> 10) & 1023, b2 = (bc >> 20) & 1023;
   const float4 xi_h = A.ph[i], xi_l = A.pl[i];
   long long out = FILL ? A.off[i] : 0;
   const long long out_end = FILL ? A.off[i + 1] : 0;
@@ -321,9 +324,8 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(NbrArgs A) {
   if (t >= A.n_atoms) return;   // whole warps leave together
   const int64_t i = A.bin_atoms[t];
   const DevCfg& C = A.cfg[A.atom_cfg[i]];
-  const long long bin = A.atom_bin[i] - C.bin_base;
-  const int b[3] = {static_cast<int>(bin / (static_cast<long long>(C.nb[1]) * C.nb[2])),
-                    static_cast<int>((bin / C.nb[2]) % C.nb[1]), static_cast<int>(bin % C.nb[2])};
+  const int bc = A.bcoord[i];
+  const int b[3] = {bc & 1023, (bc >> 10) & 1023, (bc >> 20) & 1023};
   const float4 xi_h = A.ph[i], xi_l = A.pl[i];
   const long long out0 = A.off[i], out1 = A.off[i + 1];
   const int w1 = 2 * C.kb[1] + 1, w2 = 2 * C.kb[2] + 1;
@@ -333,7 +335,8 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(NbrArgs A) {
   long long s0 = 0;
   int sz = 0;
   if (lane < n_scan) {
-    const int d[3] = {lane / (w1 * w2) - C.kb[0], (lane / w2) % w1 - C.kb[1], lane % w2 - C.kb[2]};
+    const int qd = C.qd[lane];
+    const int d[3] = {(qd & 255) - 64, ((qd >> 8) & 255) - 64, ((qd >> 16) & 255) - 64};
     int tt[3];
     bool ok = true;
     for (int a = 0; a < 3; ++a) {
@@ -551,6 +554,13 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
       if (C.kb[a] > 64) throw Fail{MTP_ERR_GEOMETRY, "cell too thin for the cut-off (more than 64 images)"};
     }
     C.K = Kmax;
+    {
+      const int v1 = 2 * C.kb[1] + 1, v2 = 2 * C.kb[2] + 1, ns = (2 * C.kb[0] + 1) * v1 * v2;
+      for (int q = 0; q < 32; ++q)
+        C.qd[q] = q < ns ? ((q / (v1 * v2) - C.kb[0] + 64) | (((q / v2) % v1 - C.kb[1] + 64) << 8) |
+                            ((q % v2 - C.kb[2] + 64) << 16))
+                         : 0;
+    }
     C.bin_base = bins;
     bins += static_cast<long long>(C.nb[0]) * C.nb[1] * C.nb[2];
     C.shift_base = static_cast<long long>(shi.size());
@@ -592,11 +602,12 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   MTP_CUDA(cudaMemcpyAsync(nb->seg.p, nb->seg_host.data(), nb->seg_host.size() * sizeof(int64_t),
                            cudaMemcpyHostToDevice, s));
   nb->atom_cfg.ensure(N * sizeof(int), s);
-  nb->wrap.ensure(N * sizeof(int) + N * sizeof(long long) + 2 * N * sizeof(float4) + 64, s);
+  nb->wrap.ensure(N * sizeof(int) + N * sizeof(long long) + 2 * N * sizeof(float4) + N * sizeof(int) + 64, s);
   int* d_wrap = nb->wrap.as<int>();
   long long* d_abin = reinterpret_cast<long long*>(reinterpret_cast<char*>(d_wrap) + ((N * sizeof(int) + 15) & ~size_t(15)));
   float4* d_ph = reinterpret_cast<float4*>(reinterpret_cast<char*>(d_abin) + ((N * sizeof(long long) + 15) & ~size_t(15)));
   float4* d_pl = d_ph + N;
+  int* d_bcoord = reinterpret_cast<int*>(d_pl + N);
   const size_t bin_bytes = (bins + 1) * (2 * sizeof(int) + sizeof(long long)) + N * sizeof(int) + 2 * N * sizeof(float4) + 256;
   nb->bins.ensure(bin_bytes, s);
   char* bp = nb->bins.as<char>();
@@ -626,6 +637,7 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.atom_cfg = nb->atom_cfg.as<int>();
   A.wrap = d_wrap;
   A.atom_bin = d_abin;
+  A.bcoord = d_bcoord;
   A.ph = d_ph;
   A.pl = d_pl;
   A.bin_count = d_bcount;

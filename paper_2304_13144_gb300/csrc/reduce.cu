@@ -106,22 +106,30 @@ __global__ void k_seg_sums(const int64_t* seg, const double* V, const double* Wa
 }
 
 __global__ void k_cfg_sums(const int64_t* seg, int64_t n_seg, const double* part, int n_cfg, double* E, double* W) {
-  // thread per config; segments of config k are contiguous in seg
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_cfg) return;
-  double acc[10];
-  for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-  // binary search first segment of config k
-  int64_t lo = 0, hi = n_seg;
+  // warp per config; the config's segments (contiguous in seg) are taken by lane s mod 32 in
+  // order, then summed over the lanes in a fixed shuffle tree
+  const int lane = threadIdx.x & 31;
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (k >= n_cfg) return;   // whole warps
+  int64_t lo = 0, hi = n_seg;   // first segment of config k
   while (lo < hi) {
     int64_t mid = (lo + hi) >> 1;
     if (seg[3 * mid] < k) lo = mid + 1; else hi = mid;
   }
-  for (int64_t s = lo; s < n_seg && seg[3 * s] == k; ++s)
+  double acc[10];
+  for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+  for (int64_t s = lo + lane; s < n_seg && seg[3 * s] == k; s += 32)
     for (int q = 0; q < 10; ++q) acc[q] += part[10 * s + q];
-  if (E) E[k] = acc[0];
-  if (W)
-    for (int q = 0; q < 9; ++q) W[9 * k + q] = acc[1 + q];
+  for (int m = 16; m; m >>= 1)
+    for (int q = 0; q < 10; ++q) {
+      const double o = __shfl_xor_sync(0xffffffffu, acc[q], m);
+      acc[q] = (lane & m) ? o + acc[q] : acc[q] + o;   // both lanes of a pair form the same sum
+    }
+  if (lane == 0) {
+    if (E) E[k] = acc[0];
+    if (W)
+      for (int q = 0; q < 9; ++q) W[9 * k + q] = acc[1 + q];
+  }
 }
 
 struct AboveThreshold {
@@ -234,7 +242,7 @@ void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, doub
   ProfRegion pr("config_sums", s);
   k_seg_sums<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), V, Wat, tmp.as<double>());
   MTP_CUDA(cudaGetLastError());
-  k_cfg_sums<<<nblk(nb->n_cfg, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, tmp.as<double>(),
+  k_cfg_sums<<<nblk(nb->n_cfg * 32, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, tmp.as<double>(),
                                                  static_cast<int>(nb->n_cfg), E, W);
   MTP_CUDA(cudaGetLastError());
 }
@@ -244,7 +252,7 @@ void run_config_sums_into(const mtp_nbr* nb, const double* V, const double* Wat,
   ProfRegion pr("config_sums", s);
   k_seg_sums<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), V, Wat, part);
   MTP_CUDA(cudaGetLastError());
-  k_cfg_sums<<<nblk(nb->n_cfg, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, part, static_cast<int>(nb->n_cfg),
+  k_cfg_sums<<<nblk(nb->n_cfg * 32, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, part, static_cast<int>(nb->n_cfg),
                                                  E, W);
   MTP_CUDA(cudaGetLastError());
 }
