@@ -226,21 +226,24 @@ __global__ void __launch_bounds__(128, 10) k_pairs(NbrArgs A) {
   for (int d0 = -C.kb[0]; d0 <= C.kb[0]; ++d0) {
     int t0 = b0 + d0, n0 = 0;
     if (C.pbc[0]) {
-        if (t0 < 0 || t0 >= C.nb[0]) { n0 = (t0 >= 0) ? t0 / C.nb[0] : -((-t0 + C.nb[0] - 1) / C.nb[0]); t0 -= n0 * C.nb[0]; }
-      }
-    else if (t0 < 0 || t0 >= C.nb[0]) continue;
+      if (t0 < 0 || t0 >= C.nb[0]) { n0 = (t0 >= 0) ? t0 / C.nb[0] : -((-t0 + C.nb[0] - 1) / C.nb[0]); t0 -= n0 * C.nb[0]; }
+    } else if (t0 < 0 || t0 >= C.nb[0]) {
+      continue;
+    }
     for (int d1 = -C.kb[1]; d1 <= C.kb[1]; ++d1) {
       int t1 = b1 + d1, n1 = 0;
       if (C.pbc[1]) {
         if (t1 < 0 || t1 >= C.nb[1]) { n1 = (t1 >= 0) ? t1 / C.nb[1] : -((-t1 + C.nb[1] - 1) / C.nb[1]); t1 -= n1 * C.nb[1]; }
+      } else if (t1 < 0 || t1 >= C.nb[1]) {
+        continue;
       }
-      else if (t1 < 0 || t1 >= C.nb[1]) continue;
       for (int d2 = -C.kb[2]; d2 <= C.kb[2]; ++d2) {
         int t2 = b2 + d2, n2 = 0;
         if (C.pbc[2]) {
-        if (t2 < 0 || t2 >= C.nb[2]) { n2 = (t2 >= 0) ? t2 / C.nb[2] : -((-t2 + C.nb[2] - 1) / C.nb[2]); t2 -= n2 * C.nb[2]; }
-      }
-        else if (t2 < 0 || t2 >= C.nb[2]) continue;
+          if (t2 < 0 || t2 >= C.nb[2]) { n2 = (t2 >= 0) ? t2 / C.nb[2] : -((-t2 + C.nb[2] - 1) / C.nb[2]); t2 -= n2 * C.nb[2]; }
+        } else if (t2 < 0 || t2 >= C.nb[2]) {
+          continue;
+        }
         const int q = ((d0 + C.kb[0]) * w1 + (d1 + C.kb[1])) * w2 + (d2 + C.kb[2]);
         if (seg)
           for (; q_next <= q; ++q_next) seg[q_next] = static_cast<uint16_t>(count);

@@ -349,9 +349,10 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
   auto finish = [&](int64_t wk, int64_t i, const float* vals, const float* grads) {
     float* const aux = P.aux_off > 0 ? const_cast<float*>(grads) + P.aux_off : aux_warp;
     float* const GMb = aux;                 // 32 x NR
-    float* const PQb = GMb + 32 * NR;       // 32 x NQ
-    int* const ZJ = reinterpret_cast<int*>(PQb + 32 * NQ);
-    float* const CB = PQb + 32 * NQ + 32;   // CBN
+    constexpr int PQS = NQ + 1;             // odd row stride: the lanes' Q_b stores hit distinct banks
+    float* const PQb = GMb + 32 * NR;       // 32 x PQS
+    int* const ZJ = reinterpret_cast<int*>(PQb + 32 * PQS);
+    float* const CB = PQb + 32 * PQS + 32;  // CBN
     if (MODE & F_ROWS) {
       for (int e = lane; e < CBN; e += 32) CB[e] = 0.f;
       __syncwarp();
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         zj = P.type[P.nb.pj[p]];
       }
       float f[NR], df[NR], g[NR];
-      radial<NR, NQ>(rr, czi + zj * NR * NQ, rmin, rcut, f, df, (MODE & F_ROWS) ? PQb + NQ * lane : nullptr);
+      radial<NR, NQ>(rr, czi + zj * NR * NQ, rmin, rcut, f, df, (MODE & F_ROWS) ? PQb + PQS * lane : nullptr);
 #pragma unroll
       for (int mu = 0; mu < NR; ++mu) g[mu] = 0.f;
       float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
           const int b = e % NQ;
           float acc = 0.f;
           for (int qq = 0; qq < nq; ++qq)
-            if (ZJ[qq] == zj2) acc = fmaf(GMb[NR * qq + mu], PQb[NQ * qq + b], acc);
+            if (ZJ[qq] == zj2) acc = fmaf(GMb[NR * qq + mu], PQb[PQS * qq + b], acc);
           CB[e] += acc;
         }
       }
@@ -659,7 +660,7 @@ bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const S
   // pair-adjoint scratch inside the finished neighborhood's adjoint array when it fits above the
   // moment adjoints, with its radial block at or above the staged row (which rewrites [0, ld))
   // and below the zero slot n_vals; otherwise one scratch block per warp
-  const int aux_head = 32 * (d.n_rad + d.n_q) + 32;   // GM, PQ, ZJ before the radial block
+  const int aux_head = 32 * (d.n_rad + d.n_q + 1) + 32;   // GM, PQ (odd stride), ZJ before the radial block
   const int aux_need = aux_head + P.CBN;
   int aux_off = std::max((d.n_mom + 3) & ~3, (P.row_stage ? static_cast<int>(o.rows_ld) : 0) - aux_head);
   aux_off = (aux_off + 3) & ~3;
