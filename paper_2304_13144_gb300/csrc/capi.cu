@@ -365,7 +365,7 @@ void run_grade_simt(mtp_model* md, int64_t N, bool fp64, const double* rows, con
                     double* gamma, int32_t* argmax, cudaStream_t s);
 bool grade_tc_available(const mtp_model* md);
 void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, int64_t ld, double* gamma,
-                  int32_t* argmax, cudaStream_t s);
+                  int32_t* argmax, const int32_t* zrow, const int64_t* row_atom, cudaStream_t s);
 
 }  // namespace mtp
 
@@ -473,13 +473,25 @@ void efs_and_grade(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, mtp_prec
     }
     o.rows_ld = ld;
   }
+  // tensor-core grade with several species: rows in species order, so that a row tile skips the
+  // radial blocks of the species it does not hold (the rows and gamma are the same)
+  const int32_t* zrow = nullptr;
+  if (use_tc && m->sched.n_types > 1) {
+    m->ws_sort.ensure(N * (sizeof(int32_t) + 2 * sizeof(int64_t)) + 64, s);
+    int64_t* order = m->ws_sort.as<int64_t>();
+    int32_t* z = reinterpret_cast<int32_t*>(order + 2 * N);
+    run_species_order(b->type, N, m->sched.n_types, z, order, m->ws_misc, s);
+    o.atom_list = order;
+    o.n_list = N;
+    zrow = z;
+  }
   run_sites(m, b, nb, fp64, o, false, nullptr, s);
   if (want_efs) {
     if (forces) run_forces(nb, fp64, o.G, forces, s);
     if (energy || virial) run_config_sums(nb, o.V, o.Wat, energy, virial, m->ws_red, s);
   }
   if (want_grade) {
-    if (use_tc) run_grade_tc(m, N, o.rows_hi, o.rows_lo, ld, gamma, argmax, s);
+    if (use_tc) run_grade_tc(m, N, o.rows_hi, o.rows_lo, ld, gamma, argmax, zrow, o.atom_list, s);
     else run_grade_simt(m, N, fp64, o.rows, o.rows_hi, ld, gamma, argmax, s);
     if (flagged || n_flagged) {
       int64_t* cnt = n_flagged;
@@ -583,8 +595,9 @@ void mtp_free_model(mtp_model* md) {
   cudaGetDevice(&cur);
   cudaSetDevice(md->device);
   cudaDeviceSynchronize();
-  for (DevBuf* b : {&md->sched_buf, &md->theta_buf, &md->ainv_d, &md->ainv_f, &md->ws_pair, &md->ws_atom,
-                    &md->ws_rows, &md->ws_misc, &md->ws_red, &md->err_flag})
+  for (DevBuf* b : {&md->sched_buf, &md->theta_buf, &md->a_d, &md->ainv_d, &md->ainv_f, &md->ws_pair,
+                    &md->ws_atom, &md->ws_rows, &md->ws_grade, &md->ws_sort, &md->ws_misc, &md->ws_red,
+                    &md->err_flag})
     b->release();
   cudaSetDevice(cur);
   delete md;
@@ -850,8 +863,8 @@ void mtp_free_nbr(mtp_nbr* nb) {
   cudaGetDevice(&cur);
   cudaSetDevice(nb->device);
   cudaDeviceSynchronize();
-  for (DevBuf* b : {&nb->off, &nb->pj, &nb->pimg, &nb->prev, &nb->pr32, &nb->atom_cfg, &nb->bins, &nb->plan,
-                    &nb->shifts, &nb->wrap, &nb->scratch, &nb->counts, &nb->seg})
+  for (DevBuf* b : {&nb->off, &nb->pj, &nb->pimg, &nb->prev, &nb->pr32, &nb->atom_cfg, &nb->segs, &nb->masks,
+                    &nb->bins, &nb->plan, &nb->shifts, &nb->wrap, &nb->scratch, &nb->counts, &nb->seg})
     b->release();
   cudaSetDevice(cur);
   delete nb;

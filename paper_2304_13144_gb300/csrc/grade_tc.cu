@@ -132,12 +132,37 @@ struct TcArgs {
   float* pbest;        // [n_pass x N] per-pass row maxima
   int32_t* parg;       // [n_pass x N] and their columns
   unsigned* err;
+  // rows grouped by the center's species (zrow[r], ascending) or zrow == null: the radial block
+  // of b_i is zero outside the center's species, so a K chunk that lies in the blocks of species
+  // absent from a tile (or in the padding past n_params) is skipped for that tile
+  const int32_t* zrow;
+  int off_c, cbn, n_params;
 };
 
+// true when every row of a tile whose species lie in [zlo, zhi] is zero in K chunk kc
+__device__ __forceinline__ bool chunk_zero(const TcArgs& a, int kc, int zlo, int zhi) {
+  if (!a.zrow) return false;
+  const int lo = kc * BK;
+  if (lo < a.off_c) return false;
+  const int hi = min(lo + BK, a.n_params) - 1;   // the chunk's last real column
+  if (hi < lo) return true;                       // padding only
+  const int z0 = (lo - a.off_c) / a.cbn, z1 = (hi - a.off_c) / a.cbn;
+  return z1 < zlo || z0 > zhi;
+}
+
+__device__ __forceinline__ void tile_species(const TcArgs& a, int64_t tile, int& zlo, int& zhi) {
+  zlo = 0;
+  zhi = 0;
+  if (!a.zrow) return;
+  zlo = a.zrow[tile * BM];
+  zhi = a.zrow[min(a.N, (tile + 1) * BM) - 1];
+}
+
 // gamma_i and argmax_i from the per-pass partials: passes in column order, strict '>' keeps the
-// lowest column on ties; a NaN partial (a pass that did not run) makes gamma_i NaN
-__global__ void k_grade_combine(int64_t N, int n_pass, const float* pbest, const int32_t* parg, double* gamma,
-                                int32_t* argmax) {
+// lowest column on ties; a NaN partial (a pass that did not run) makes gamma_i NaN; row r is atom
+// row_atom[r] when rows were grouped by species
+__global__ void k_grade_combine(int64_t N, int n_pass, const float* pbest, const int32_t* parg, const int64_t* row_atom,
+                                double* gamma, int32_t* argmax) {
   const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (r >= N) return;
   float best = -1.f;
@@ -148,8 +173,9 @@ __global__ void k_grade_combine(int64_t N, int n_pass, const float* pbest, const
     nan = nan || (v != v);
     if (v > best) { best = v; arg = parg[p * N + r]; }
   }
-  gamma[r] = nan ? __longlong_as_double(0x7ff8000000000000LL) : static_cast<double>(best);
-  if (argmax) argmax[r] = arg;
+  const int64_t o = row_atom ? row_atom[r] : r;
+  gamma[o] = nan ? __longlong_as_double(0x7ff8000000000000LL) : static_cast<double>(best);
+  if (argmax) argmax[o] = arg;
 }
 
 __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__ CUtensorMap mAh,
@@ -195,7 +221,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
       for (int64_t w = blockIdx.x; w < a.n_work && !*abort_flag; w += gridDim.x) {
         const int64_t tile = w / a.n_pass;
         const int pass = static_cast<int>(w - tile * a.n_pass);
-          for (int kc = 0; kc < a.k_chunks; ++kc, ++it) {
+        int zlo, zhi;
+        tile_species(a, tile, zlo, zhi);
+          for (int kc = 0; kc < a.k_chunks; ++kc) {
+            if (chunk_zero(a, kc, zlo, zhi)) continue;
             const uint32_t s = it % STAGES, n = it / STAGES;
             if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag)) { *abort_flag = 1; break; }
             unsigned char* st = ring + s * STAGE_BYTES;
@@ -205,6 +234,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
             tma_load_2d(st + A_BYTES, &mAl, x, yr, &full[s]);
             tma_load_2d(st + 2 * A_BYTES, &mBh, x, yc, &full[s]);
             tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mBl, x, yc, &full[s]);
+            ++it;
           }
       }
       if (*abort_flag) {
@@ -227,7 +257,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
           if (na > 0 && !mbar_wait(&acce[b], (na - 1) & 1, abort_flag)) { *abort_flag = 1; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t dtm = tmem + b * BN;
-          for (int kc = 0; kc < a.k_chunks; ++kc, ++it) {
+          int zlo, zhi;
+          tile_species(a, w / a.n_pass, zlo, zhi);
+          for (int kc = 0; kc < a.k_chunks; ++kc) {
+            if (chunk_zero(a, kc, zlo, zhi)) continue;   // chunk 0 never is: the first MMA sets D
             const uint32_t s = it % STAGES, n = it / STAGES;
             if (!mbar_wait(&full[s], n & 1, abort_flag)) { *abort_flag = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -243,6 +276,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
             }
             mma_commit(&empty[s]);
             issued = true;
+            ++it;
           }
           if (*abort_flag) break;
           mma_commit(&accf[b]);
@@ -348,7 +382,7 @@ bool grade_tc_available(const mtp_model* md) {
 }
 
 void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, int64_t ld, double* gamma,
-                  int32_t* argmax, cudaStream_t s) {
+                  int32_t* argmax, const int32_t* zrow, const int64_t* row_atom, cudaStream_t s) {
   if (N == 0) return;
   if (ld != md->ainv_ld || ld % BN != 0) throw Fail{MTP_ERR_ARG, "grade: row stride mismatch"};
   const float* xh = md->ainv_f.as<float>();
@@ -370,6 +404,10 @@ void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, in
   // partials start as NaN: a pass that does not run (a bounded wait expired) leaves gamma NaN
   MTP_CUDA(cudaMemsetAsync(a.pbest, 0xFF, static_cast<size_t>(a.n_pass) * N * sizeof(float), s));
   a.err = md->err_flag.as<unsigned>();
+  a.zrow = zrow;
+  a.off_c = md->sched.n_types + md->sched.n_lin;
+  a.cbn = md->sched.n_types * md->sched.n_rad * md->sched.n_q;
+  a.n_params = md->sched.n_params;
   MTP_CUDA(cudaFuncSetAttribute(k_grade_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(SMEM_BYTES)));
   int nsm = 0;
   MTP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, md->device));
@@ -378,7 +416,8 @@ void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, in
   ProfRegion pr("grade_tc_tf32x3", s);
   k_grade_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, a);
   MTP_CUDA(cudaGetLastError());
-  k_grade_combine<<<static_cast<unsigned>((N + 255) / 256), 256, 0, s>>>(N, a.n_pass, a.pbest, a.parg, gamma, argmax);
+  k_grade_combine<<<static_cast<unsigned>((N + 255) / 256), 256, 0, s>>>(N, a.n_pass, a.pbest, a.parg, row_atom,
+                                                                         gamma, argmax);
   MTP_CUDA(cudaGetLastError());
 }
 

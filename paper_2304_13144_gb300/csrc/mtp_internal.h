@@ -168,6 +168,7 @@ struct mtp_model {
   mtp::DevBuf ws_atom;         // per-atom V, W
   mtp::DevBuf ws_rows;         // parameter rows for the grade
   mtp::DevBuf ws_grade;        // per-pass partial row maxima of the tensor-core grade
+  mtp::DevBuf ws_sort;         // species order of the rows for the tensor-core grade
   mtp::DevBuf ws_misc;
   mtp::DevBuf ws_red;          // reductions
   mtp::DevBuf err_flag;        // unsigned
@@ -227,6 +228,10 @@ struct SiteOutputs {
 void run_sites(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, bool fp64, const SiteOutputs& o,
                bool tangent, int* grid_used, cudaStream_t s);
 void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStream_t s);
+// atom indices sorted (stably) by species into order[0, N) (order needs 2N entries) and their
+// species into zrow
+void run_species_order(const int32_t* type, int64_t N, int n_types, int32_t* zrow, int64_t* order, DevBuf& tmp,
+                       cudaStream_t s);
 void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, double* E, double* W,
                      DevBuf& tmp, cudaStream_t s);
 void run_lu_inverse(mtp_model* m, const double* A, int64_t n, cudaStream_t s);

@@ -257,6 +257,27 @@ void run_config_sums_into(const mtp_nbr* nb, const double* V, const double* Wat,
   MTP_CUDA(cudaGetLastError());
 }
 
+namespace {
+__global__ void k_iota64(int64_t n, int64_t* out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i < n) out[i] = i;
+}
+}  // namespace
+
+void run_species_order(const int32_t* type, int64_t N, int n_types, int32_t* zrow, int64_t* order, DevBuf& tmp,
+                       cudaStream_t s) {
+  // a stable radix sort of the atom indices by species (ties keep index order)
+  int bits = 1;
+  while ((1 << bits) < n_types) ++bits;
+  int64_t* iota = order + N;   // the caller provides 2N entries
+  k_iota64<<<nblk(N, 256), 256, 0, s>>>(N, iota);
+  MTP_CUDA(cudaGetLastError());
+  size_t bytes = 0;
+  MTP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, type, zrow, iota, order, static_cast<int>(N), 0, bits, s));
+  tmp.ensure(bytes, s);
+  MTP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, bytes, type, zrow, iota, order, static_cast<int>(N), 0, bits, s));
+}
+
 void run_flag(int64_t N, const double* gamma, double threshold, int32_t* flagged, int64_t* n_flagged, DevBuf& tmp,
               cudaStream_t s) {
   AboveThreshold pred{gamma, threshold};
