@@ -473,16 +473,18 @@ void efs_and_grade(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, mtp_prec
     }
     o.rows_ld = ld;
   }
-  // tensor-core grade with several species: rows in species order, so that a row tile skips the
-  // radial blocks of the species it does not hold (the rows and gamma are the same)
+  // tensor-core grade with several species: the rows are stored in species order (the
+  // neighborhoods are still evaluated in atom order), so that a row tile skips the radial blocks
+  // of the species it does not hold; b_i and gamma_i are the same
   const int32_t* zrow = nullptr;
+  const int64_t* row_atom = nullptr;
   if (use_tc && m->sched.n_types > 1) {
     m->ws_sort.ensure(N * (sizeof(int32_t) + 2 * sizeof(int64_t)) + 64, s);
     int64_t* order = m->ws_sort.as<int64_t>();
     int32_t* z = reinterpret_cast<int32_t*>(order + 2 * N);
     run_species_order(b->type, N, m->sched.n_types, z, order, m->ws_misc, s);
-    o.atom_list = order;
-    o.n_list = N;
+    o.row_pos = order + N;
+    row_atom = order;
     zrow = z;
   }
   run_sites(m, b, nb, fp64, o, false, nullptr, s);
@@ -491,7 +493,7 @@ void efs_and_grade(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, mtp_prec
     if (energy || virial) run_config_sums(nb, o.V, o.Wat, energy, virial, m->ws_red, s);
   }
   if (want_grade) {
-    if (use_tc) run_grade_tc(m, N, o.rows_hi, o.rows_lo, ld, gamma, argmax, zrow, o.atom_list, s);
+    if (use_tc) run_grade_tc(m, N, o.rows_hi, o.rows_lo, ld, gamma, argmax, zrow, row_atom, s);
     else run_grade_simt(m, N, fp64, o.rows, o.rows_hi, ld, gamma, argmax, s);
     if (flagged || n_flagged) {
       int64_t* cnt = n_flagged;

@@ -217,6 +217,7 @@ struct SiteOutputs {
   float* rows_lo = nullptr;
   int64_t rows_ld = 0;
   const int64_t* atom_list = nullptr;  // optional explicit atoms (rows follow list order)
+  const int64_t* row_pos = nullptr;    // optional row of each atom's b_i (rows in another order)
   int64_t n_list = 0;
   // tangent mode (training)
   const double* U = nullptr;    // per atom 3
@@ -228,8 +229,8 @@ struct SiteOutputs {
 void run_sites(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, bool fp64, const SiteOutputs& o,
                bool tangent, int* grid_used, cudaStream_t s);
 void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStream_t s);
-// atom indices sorted (stably) by species into order[0, N) (order needs 2N entries) and their
-// species into zrow
+// atom indices sorted (stably) by species into order[0, N), their species into zrow, and each
+// atom's position in that order into order[N, 2N)
 void run_species_order(const int32_t* type, int64_t N, int n_types, int32_t* zrow, int64_t* order, DevBuf& tmp,
                        cudaStream_t s);
 void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, double* E, double* W,

@@ -262,6 +262,10 @@ __global__ void k_iota64(int64_t n, int64_t* out) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i < n) out[i] = i;
 }
+__global__ void k_rank64(int64_t n, const int64_t* order, int64_t* rank) {
+  const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (r < n) rank[order[r]] = r;
+}
 }  // namespace
 
 void run_species_order(const int32_t* type, int64_t N, int n_types, int32_t* zrow, int64_t* order, DevBuf& tmp,
@@ -276,6 +280,8 @@ void run_species_order(const int32_t* type, int64_t N, int n_types, int32_t* zro
   MTP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, type, zrow, iota, order, static_cast<int>(N), 0, bits, s));
   tmp.ensure(bytes, s);
   MTP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, bytes, type, zrow, iota, order, static_cast<int>(N), 0, bits, s));
+  k_rank64<<<nblk(N, 256), 256, 0, s>>>(N, order, order + N);   // the sort's input is no longer needed
+  MTP_CUDA(cudaGetLastError());
 }
 
 void run_flag(int64_t N, const double* gamma, double threshold, int32_t* flagged, int64_t* n_flagged, DevBuf& tmp,

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kWarps * 32) site_kernel(SiteParams P) {
         for (int k = 0; k < 9; ++k) P.o.Wat[9 * i + k] = Wacc[k];
     }
     if (MODE & M_ROWS) {
-      const int64_t row = wk;
+      const int64_t row = P.o.row_pos ? P.o.row_pos[i] : wk;
       const int64_t ld = P.o.rows_ld;
       const int cb_total = T * L.CBN;
       if (P.o.rows) {

@@ -435,11 +435,12 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
         if (lane == 0) P.o.Wat[9 * i + k] = static_cast<double>(v);
       }
     }
+    const int64_t rw = P.o.row_pos ? P.o.row_pos[i] : wk;   // this neighborhood's row of b
     if ((MODE & F_ROWS) && !P.row_stage) {
       const int64_t ld = P.o.rows_ld;
-      float* hi = P.o.rows_hi ? P.o.rows_hi + wk * ld : nullptr;
-      float* lo = P.o.rows_lo ? P.o.rows_lo + wk * ld : nullptr;
-      double* out64 = P.o.rows ? P.o.rows + wk * ld : nullptr;
+      float* hi = P.o.rows_hi ? P.o.rows_hi + rw * ld : nullptr;
+      float* lo = P.o.rows_lo ? P.o.rows_lo + rw * ld : nullptr;
+      double* out64 = P.o.rows ? P.o.rows + rw * ld : nullptr;
       auto put = [&](int64_t k, float v) {
         if (out64) out64[k] = v;
         if (hi) {
@@ -470,12 +471,12 @@ __global__ void __launch_bounds__(kMaxWarpsF * 32, 1) site_fast_kernel(FastParam
       for (int e = lane; e < CBN; e += 32) row[off_c + zi * CBN + e] = CB[e];
       __syncwarp();
       if (P.o.rows) {
-        double* out64 = P.o.rows + wk * ld;
+        double* out64 = P.o.rows + rw * ld;
         for (int k = lane; k < d.n_params; k += 32) out64[k] = row[k];
       }
       if (P.o.rows_hi) {
-        float4* hi = reinterpret_cast<float4*>(P.o.rows_hi + wk * ld);
-        float4* lo = P.o.rows_lo ? reinterpret_cast<float4*>(P.o.rows_lo + wk * ld) : nullptr;
+        float4* hi = reinterpret_cast<float4*>(P.o.rows_hi + rw * ld);
+        float4* lo = P.o.rows_lo ? reinterpret_cast<float4*>(P.o.rows_lo + rw * ld) : nullptr;
         const float4* src = reinterpret_cast<const float4*>(row);
         for (int k = lane; k < ld / 4; k += 32) {
           const float4 v = src[k];
