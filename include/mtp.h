@@ -361,8 +361,9 @@ mtp_status mtp_profiler_enable(int on);
 
 /* Synchronise the recorded events, then report per region name (in order of first
  * appearance, at most `capacity` regions): names[48*k] (NUL-terminated), total device
- * time ms[k] and number of launches launches[k]; *count = regions written.  Clears the
- * record.  Host arrays; any of names/ms/launches may be NULL. */
+ * time ms[k] and launches[k] = launches of the library's own kernels inside the region (the
+ * CUB scan, sort and select kernels it also runs are not counted); *count = regions written.
+ * Clears the record.  Host arrays; any of names/ms/launches may be NULL. */
 mtp_status mtp_profiler_read(int32_t capacity, char* names, double* ms, int64_t* launches, int32_t* count);
 
 #ifdef __cplusplus

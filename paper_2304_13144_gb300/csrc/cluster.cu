@@ -176,6 +176,7 @@ int64_t run_cut_clusters(const mtp_batch* b, const int64_t* centers, int64_t n, 
   const unsigned g = static_cast<unsigned>(std::max<int64_t>(1, (n + 7) / 8));
   ProfRegion pr("cut_clusters", s);
   k_cut<false><<<g, 256, 0, s>>>(A);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   // offsets: exclusive scan of the counts into off[0..n]
   DevBuf scan_tmp;
@@ -196,6 +197,7 @@ int64_t run_cut_clusters(const mtp_batch* b, const int64_t* centers, int64_t n, 
   A.out_type = type;
   A.out_src = src;
   k_cut<true><<<g, 256, 0, s>>>(A);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   MTP_CUDA(cudaMemcpyAsync(&flag, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MTP_CUDA(cudaStreamSynchronize(s));

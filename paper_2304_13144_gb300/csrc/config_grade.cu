@@ -107,9 +107,13 @@ void run_config_row_sums(const mtp_nbr* nb, const double* rows, int64_t m, doubl
   tmp.ensure(static_cast<size_t>(nb->n_seg) * m * sizeof(double), s);
   ProfRegion pr("config_rows_sum", s);
   const dim3 g(static_cast<unsigned>(nb->n_seg), blocks(m, 128));
-  if (nb->n_seg > 0) k_seg_row_sums<<<g, 128, 0, s>>>(nb->seg.as<int64_t>(), rows, m, tmp.as<double>());
+  if (nb->n_seg > 0) {
+    k_seg_row_sums<<<g, 128, 0, s>>>(nb->seg.as<int64_t>(), rows, m, tmp.as<double>());
+    ProfRegion::launched();
+  }
   k_cfg_row_sums<<<blocks(nb->n_cfg * m, 256), 256, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, tmp.as<double>(), m,
                                                            nb->n_cfg, out);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 
@@ -119,21 +123,27 @@ void run_config_gamma_max(const mtp_nbr* nb, const double* gamma, double* gamma_
   double* gmax = tmp.as<double>();
   int64_t* amax = reinterpret_cast<int64_t*>(gmax + std::max<int64_t>(nb->n_seg, 1));
   ProfRegion pr("config_gamma_max", s);
-  if (nb->n_seg > 0) k_seg_gamma_max<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), gamma, gmax, amax);
+  if (nb->n_seg > 0) {
+    k_seg_gamma_max<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), gamma, gmax, amax);
+    ProfRegion::launched();
+  }
   k_cfg_gamma_max<<<blocks(nb->n_cfg, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, gmax, amax, nb->n_cfg,
                                                         gamma_cfg, worst);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 
 void run_classify(const double* gamma, int64_t n, double g_save, double g_break, int32_t* cls, cudaStream_t s) {
   if (n == 0) return;
   k_classify<<<blocks(n, 256), 256, 0, s>>>(gamma, n, g_save, g_break, cls);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 
 void run_widen_argmax(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s) {
   if (n == 0) return;
   k_widen_argmax<<<blocks(n, 256), 256, 0, s>>>(in, n, out);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 

@@ -205,6 +205,7 @@ extern "C" mtp_status mtp_fit_errors(mtp_model* md, const mtp_batch* b, const mt
     check(mtp_energy_forces_stress(md, b, nb, prec, E, nullptr, F, W, stream));
     if (N > 0) {
       k_force_err<<<kErrBlocks, 256, 0, s>>>(F, F_ref, N, part);
+      ProfRegion::launched();
       MTP_CUDA(cudaGetLastError());
     }
     MTP_CUDA(cudaMemcpyAsync(Er, E_ref, K * sizeof(double), cudaMemcpyDeviceToDevice, s));

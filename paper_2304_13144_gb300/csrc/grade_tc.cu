@@ -415,9 +415,11 @@ void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, in
   const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(a.n_work, per)));
   ProfRegion pr("grade_tc_tf32x3", s);
   k_grade_tc<<<grid, THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, a);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   k_grade_combine<<<static_cast<unsigned>((N + 255) / 256), 256, 0, s>>>(N, a.n_pass, a.pbest, a.parg, row_atom,
                                                                          gamma, argmax);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 

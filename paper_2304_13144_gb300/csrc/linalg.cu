@@ -202,18 +202,23 @@ void run_lu_inverse(mtp_model* md, const double* A, int64_t m, cudaStream_t s) {
   MTP_CUDA(cudaMemcpyAsync(LU, A, m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
   ProfRegion pr("active_set_lu_inverse", s);
   k_maxabs<<<1, 1024, 0, s>>>(A, m * m, md->ws_misc.as<double>());
+  ProfRegion::launched();
   for (int64_t k = 0; k < m; ++k) {
     k_pivot<<<1, 1024, 0, s>>>(LU, m, k, piv, md->ws_misc.as<double>(), md->err_flag.as<unsigned>());
+    ProfRegion::launched();
     const int64_t rem = m - k - 1;
     if (rem > 0) {
       k_lcol<<<static_cast<unsigned>((rem + 255) / 256), 256, 0, s>>>(LU, m, k);
+      ProfRegion::launched();
       dim3 g(static_cast<unsigned>((rem + 127) / 128), static_cast<unsigned>(rem));
       k_trail<<<g, 128, 0, s>>>(LU, m, k);
+      ProfRegion::launched();
     }
   }
   MTP_CUDA(cudaGetLastError());
   md->ainv_d.ensure(m * m * sizeof(double), s);
   k_inverse_cols<<<static_cast<unsigned>((m + 63) / 64), 64, 0, s>>>(LU, piv, m, md->ainv_d.as<double>());
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   // mixed-path copies: K-major padded split (tensor cores) and plain FP32 (SIMT)
   const int64_t ld = grade_tc_ld(m);
@@ -221,7 +226,9 @@ void run_lu_inverse(mtp_model* md, const double* A, int64_t m, cudaStream_t s) {
   md->ainv_f.ensure((2 * ld * ld + m * m) * sizeof(float), s);
   float* hi = md->ainv_f.as<float>();
   k_split_ainv<<<static_cast<unsigned>((ld * ld + 255) / 256), 256, 0, s>>>(md->ainv_d.as<double>(), m, ld, hi, hi + ld * ld);
+  ProfRegion::launched();
   k_to_float<<<static_cast<unsigned>((m * m + 255) / 256), 256, 0, s>>>(md->ainv_d.as<double>(), m * m, hi + 2 * ld * ld);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   unsigned flag = 0;
   MTP_CUDA(cudaMemcpyAsync(&flag, md->err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -238,9 +245,14 @@ void run_grade_simt(mtp_model* md, int64_t N, bool fp64, const double* rows, con
   const unsigned g = static_cast<unsigned>((N + 63) / 64);
   if (N == 0) return;
   ProfRegion pr(fp64 ? "grade_simt_fp64" : "grade_simt_fp32", s);
-  if (fp64) k_grade_simt<double><<<g, 256, 0, s>>>(rows, ld, md->ainv_d.as<double>(), m, N, gamma, argmax);
-  else k_grade_simt<float><<<g, 256, 0, s>>>(rows_f, ld, md->ainv_f.as<float>() + 2 * md->ainv_ld * md->ainv_ld, m, N,
-                                             gamma, argmax);
+  if (fp64) {
+    k_grade_simt<double><<<g, 256, 0, s>>>(rows, ld, md->ainv_d.as<double>(), m, N, gamma, argmax);
+    ProfRegion::launched();
+  } else {
+    k_grade_simt<float><<<g, 256, 0, s>>>(rows_f, ld, md->ainv_f.as<float>() + 2 * md->ainv_ld * md->ainv_ld, m, N,
+                                               gamma, argmax);
+    ProfRegion::launched();
+  }
   MTP_CUDA(cudaGetLastError());
 }
 

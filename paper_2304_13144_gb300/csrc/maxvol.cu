@@ -170,6 +170,7 @@ int64_t run_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_
       const dim3 grd(static_cast<unsigned>((m + GT - 1) / GT),
                      static_cast<unsigned>(std::min<int64_t>((n + GT - 1) / GT, 65535)));
       k_gemm<<<grd, blk, 0, s>>>(B, md->ainv_d.as<double>(), C, n, static_cast<int>(m));
+      ProfRegion::launched();
       MTP_CUDA(cudaGetLastError());
     }
     const long long total = static_cast<long long>(n) * m;
@@ -179,7 +180,9 @@ int64_t run_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_
     Best best{};
     while (swaps < max_swaps) {
       k_argmax_part<<<n_part, 256, 0, s>>>(C, total, part);
+      ProfRegion::launched();
       k_argmax_final<<<1, 1024, 0, s>>>(part, n_part, best_d);
+      ProfRegion::launched();
       MTP_CUDA(cudaGetLastError());
       MTP_CUDA(cudaMemcpyAsync(&best, best_d, sizeof(Best), cudaMemcpyDeviceToHost, s));
       MTP_CUDA(cudaStreamSynchronize(s));
@@ -188,8 +191,11 @@ int64_t run_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_
       const int j = static_cast<int>(best.idx - i * m);
       k_swap_vectors<<<g_v, 256, 0, s>>>(C, md->ainv_d.as<double>(), B, md->a_d.as<double>(), n, static_cast<int>(m),
                                          i, j, u, v, w);
+      ProfRegion::launched();
       k_rank1<<<g_nm, 256, 0, s>>>(C, n, static_cast<int>(m), v, u);
+      ProfRegion::launched();
       k_rank1<<<g_mm, 256, 0, s>>>(md->ainv_d.as<double>(), m, static_cast<int>(m), w, u);
+      ProfRegion::launched();
       MTP_CUDA(cudaGetLastError());
       src[static_cast<size_t>(j)] = i;
       ++swaps;

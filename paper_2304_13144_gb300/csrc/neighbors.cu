@@ -655,26 +655,30 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   nb->masks.ensure(static_cast<size_t>(N) * kMaskWords * sizeof(uint32_t), s);
   A.mask = nb->masks.as<uint32_t>();
   const int TB = 256;
-  ProfRegion* pr1 = new ProfRegion("neighbors_bin_count", s);
-  k_prep<<<blocks_for(N, TB), TB, 0, s>>>(A);
-  MTP_CUDA(cudaGetLastError());
-  // bin_count has bins+1 entries (last = 0) -> bin_start[bins] = N
   {
-    // scan int counts into long long starts
-    std::vector<int> dummy;
-    size_t bytes = 0;
-    MTP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, d_bcount, d_bstart, bins + 1, s));
-    nb->scratch.ensure(bytes, s);
-    MTP_CUDA(cub::DeviceScan::ExclusiveSum(nb->scratch.p, bytes, d_bcount, d_bstart, bins + 1, s));
+    ProfRegion pr1("neighbors_bin_count", s);
+    k_prep<<<blocks_for(N, TB), TB, 0, s>>>(A);
+    ProfRegion::launched();
+    MTP_CUDA(cudaGetLastError());
+    // bin_count has bins+1 entries (last = 0) -> bin_start[bins] = N
+    {
+      // scan int counts into long long starts
+      size_t bytes = 0;
+      MTP_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, d_bcount, d_bstart, bins + 1, s));
+      nb->scratch.ensure(bytes, s);
+      MTP_CUDA(cub::DeviceScan::ExclusiveSum(nb->scratch.p, bytes, d_bcount, d_bstart, bins + 1, s));
+    }
+    k_scatter<<<blocks_for(N, TB), TB, 0, s>>>(A);
+    ProfRegion::launched();
+    MTP_CUDA(cudaGetLastError());
+    k_sort_bins<<<blocks_for(bins, TB), TB, 0, s>>>(A, bins);
+    ProfRegion::launched();
+    MTP_CUDA(cudaGetLastError());
+    k_pairs<false><<<blocks_for(N, 128), 128, 0, s>>>(A);
+    ProfRegion::launched();
+    MTP_CUDA(cudaGetLastError());
+    scan_exclusive<long long>(nb->counts.as<long long>(), nb->off.as<long long>(), N + 1, nb->scratch, s);
   }
-  k_scatter<<<blocks_for(N, TB), TB, 0, s>>>(A);
-  MTP_CUDA(cudaGetLastError());
-  k_sort_bins<<<blocks_for(bins, TB), TB, 0, s>>>(A, bins);
-  MTP_CUDA(cudaGetLastError());
-  k_pairs<false><<<blocks_for(N, 128), 128, 0, s>>>(A);
-  MTP_CUDA(cudaGetLastError());
-  scan_exclusive<long long>(nb->counts.as<long long>(), nb->off.as<long long>(), N + 1, nb->scratch, s);
-  delete pr1;
   long long total = 0;
   unsigned flag = 0;
   MTP_CUDA(cudaMemcpyAsync(&total, nb->off.as<long long>() + N, sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -711,13 +715,19 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   for (int attempt = 0;; ++attempt) {
     {
       ProfRegion pr2("neighbors_fill", s);
-      if (A.seg) k_fill_warp<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
-      else k_pairs<true><<<blocks_for(N, 128), 128, 0, s>>>(A);
+      if (A.seg) {
+        k_fill_warp<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
+        ProfRegion::launched();
+      } else {
+        k_pairs<true><<<blocks_for(N, 128), 128, 0, s>>>(A);
+        ProfRegion::launched();
+      }
       MTP_CUDA(cudaGetLastError());
     }
     if (total > 0) {
       ProfRegion pr3("neighbors_reverse", s);
       k_reverse<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
+      ProfRegion::launched();
       MTP_CUDA(cudaGetLastError());
     }
     MTP_CUDA(cudaMemcpyAsync(&flag, m->err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

@@ -1,6 +1,7 @@
 // Kernel-level tracing: when enabled, every launch region records a CUDA event pair on the
-// stream it is launched on; mtp_profiler_read() synchronises, accumulates device time and the
-// number of launches per region name, and clears the record.
+// stream it is launched on and counts the library's own kernels launched inside it;
+// mtp_profiler_read() synchronises, accumulates device time and kernel launches per region name,
+// and clears the record.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -20,7 +21,9 @@ namespace {
 struct Rec {
   const char* name;
   cudaEvent_t a, b;
+  int kernels;
 };
+thread_local ProfRegion* t_open = nullptr;   // innermost open region of this thread
 std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
@@ -39,7 +42,8 @@ cudaEvent_t take() {
 
 }  // namespace
 
-ProfRegion::ProfRegion(const char* name, cudaStream_t s) : name_(name), s_(s) {
+ProfRegion::ProfRegion(const char* name, cudaStream_t s) : name_(name), s_(s), outer_(t_open) {
+  t_open = this;
   nvtxRangePushA(name);   // host-side range for timeline tools (a no-op without one attached)
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on) return;
@@ -49,11 +53,16 @@ ProfRegion::ProfRegion(const char* name, cudaStream_t s) : name_(name), s_(s) {
 }
 
 ProfRegion::~ProfRegion() {
+  t_open = outer_;
   nvtxRangePop();
   std::lock_guard<std::mutex> lk(g_mu);
   if (!a_ || !b_) return;
   cudaEventRecord(b_, s_);
-  g_recs.push_back({name_, a_, b_});
+  g_recs.push_back({name_, a_, b_, kernels_});
+}
+
+void ProfRegion::launched() {
+  if (t_open) ++t_open->kernels_;
 }
 
 }  // namespace mtp
@@ -86,7 +95,7 @@ mtp_status mtp_profiler_read(int32_t capacity, char* names, double* ms, int64_t*
     auto it = acc.find(r.name);
     if (it == acc.end()) { order.push_back(r.name); acc[r.name] = {0.0, 0}; }
     acc[r.name].first += t;
-    acc[r.name].second += 1;
+    acc[r.name].second += r.kernels;
   }
   {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -231,8 +231,13 @@ __global__ void k_sum_rows(const double* part, int nrows, int64_t m, double* out
 
 void run_forces(const mtp_nbr* nb, bool fp64, const void* G, double* F, cudaStream_t s) {
   ProfRegion pr("force_gather", s);
-  if (fp64) k_forces<<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const double*>(G), F);
-  else k_forces_grp<8><<<nblk(nb->n_atoms * 8, 256), 256, 0, s>>>(nb->dn, static_cast<const float*>(G), F);
+  if (fp64) {
+    k_forces<<<nblk(nb->n_atoms, 256), 256, 0, s>>>(nb->dn, static_cast<const double*>(G), F);
+    ProfRegion::launched();
+  } else {
+    k_forces_grp<8><<<nblk(nb->n_atoms * 8, 256), 256, 0, s>>>(nb->dn, static_cast<const float*>(G), F);
+    ProfRegion::launched();
+  }
   MTP_CUDA(cudaGetLastError());
 }
 
@@ -241,9 +246,11 @@ void run_config_sums(const mtp_nbr* nb, const double* V, const double* Wat, doub
   tmp.ensure(nb->n_seg * 10 * sizeof(double), s);
   ProfRegion pr("config_sums", s);
   k_seg_sums<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), V, Wat, tmp.as<double>());
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   k_cfg_sums<<<nblk(nb->n_cfg * 32, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, tmp.as<double>(),
                                                  static_cast<int>(nb->n_cfg), E, W);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 
@@ -251,9 +258,11 @@ void run_config_sums_into(const mtp_nbr* nb, const double* V, const double* Wat,
                           cudaStream_t s) {
   ProfRegion pr("config_sums", s);
   k_seg_sums<<<static_cast<unsigned>(nb->n_seg), 256, 0, s>>>(nb->seg.as<int64_t>(), V, Wat, part);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   k_cfg_sums<<<nblk(nb->n_cfg * 32, 128), 128, 0, s>>>(nb->seg.as<int64_t>(), nb->n_seg, part, static_cast<int>(nb->n_cfg),
                                                  E, W);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 
@@ -271,16 +280,19 @@ __global__ void k_rank64(int64_t n, const int64_t* order, int64_t* rank) {
 void run_species_order(const int32_t* type, int64_t N, int n_types, int32_t* zrow, int64_t* order, DevBuf& tmp,
                        cudaStream_t s) {
   // a stable radix sort of the atom indices by species (ties keep index order)
+  ProfRegion pr("grade_row_order", s);
   int bits = 1;
   while ((1 << bits) < n_types) ++bits;
   int64_t* iota = order + N;   // the caller provides 2N entries
   k_iota64<<<nblk(N, 256), 256, 0, s>>>(N, iota);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   size_t bytes = 0;
   MTP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, type, zrow, iota, order, static_cast<int>(N), 0, bits, s));
   tmp.ensure(bytes, s);
   MTP_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, bytes, type, zrow, iota, order, static_cast<int>(N), 0, bits, s));
   k_rank64<<<nblk(N, 256), 256, 0, s>>>(N, order, order + N);   // the sort's input is no longer needed
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 
@@ -302,6 +314,7 @@ int64_t run_extract(const mtp_nbr* nb, const mtp_batch* b, const int32_t* idx, i
   unsigned* bad = reinterpret_cast<unsigned*>(cnt + n + 1);
   MTP_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), s));
   k_extract_counts<<<nblk(n + 1, 256), 256, 0, s>>>(nb->dn, idx, n, cnt, bad);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   DevBuf scan_tmp;
   size_t bytes = 0;
@@ -319,6 +332,7 @@ int64_t run_extract(const mtp_nbr* nb, const mtp_batch* b, const int32_t* idx, i
   if (total > capacity) return total;
   if (n > 0) {
     k_extract_fill<<<nblk(n, 128), 128, 0, s>>>(nb->dn, b->pos, b->type, b->cell, idx, n, offl, r, type, j);
+    ProfRegion::launched();
     MTP_CUDA(cudaGetLastError());
   }
   return total;
@@ -331,14 +345,17 @@ void run_train_prep(const mtp_nbr* nb, int n_cfg, const double* E, const double*
   tmp.ensure(nb_f * sizeof(double), s);
   ProfRegion pr("train_residuals", s);
   k_train_forces<<<nb_f, 256, 0, s>>>(nb->n_atoms, F, F_ref, w_f, U, tmp.as<double>());
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   k_train_cfg<<<1, 256, 0, s>>>(n_cfg, E, E_ref, W, W_ref, w_e, w_f, w_s, tmp.as<double>(), nb_f, coef, Scfg, loss);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 
 void run_sum_rows(const double* part, int nrows, int64_t m, double* out, cudaStream_t s) {
   ProfRegion pr("train_grad_sum", s);
   k_sum_rows<<<nblk(m, 128), 128, 0, s>>>(part, nrows, m, out);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 

@@ -164,8 +164,7 @@ __device__ __forceinline__ void pair_setup(const SiteParams& P, const R* ctab, i
   for (int b = 0; b < L.NQ; ++b) {
     S tb, db;
     if (b == 0) { tb = t0; db = d0; }
-    else if (b == 1) { tb = t1; db = d1; }
-    else {
+    else if (b == 1) { tb = t1; db = d1; } else {
       S t2 = R(2) * x * t1 - t0;
       S d2 = R(2) * t1 + R(2) * x * d1 - d0;
       t0 = t1; t1 = t2; d0 = d1; d1 = d2;
@@ -210,8 +209,7 @@ __global__ void __launch_bounds__(kWarps * 32) site_kernel(SiteParams P) {
   const R* tri_c = nullptr;
   const R* use_c = nullptr;
   const R* seed = nullptr;
-  if constexpr (std::is_same<R, float>::value) { theta = d.theta_f; tri_c = d.tri_cf; use_c = d.use_cf; seed = d.seed_f; }
-  else { theta = d.theta_d; tri_c = d.tri_cd; use_c = d.use_cd; seed = d.seed_d; }
+  if constexpr (std::is_same<R, float>::value) { theta = d.theta_f; tri_c = d.tri_cf; use_c = d.use_cf; seed = d.seed_f; } else { theta = d.theta_d; tri_c = d.tri_cd; use_c = d.use_cd; seed = d.seed_d; }
   const int T = d.n_types;
   const int64_t off_c = T + d.n_lin;
   for (int k = threadIdx.x; k < L.NC; k += blockDim.x) ctab[k] = theta[off_c + k];
@@ -479,6 +477,7 @@ int launch_sites(const SiteParams& P0, int* grid_used, cudaStream_t s) {
   const char* name = (MODE & M_TAN) ? "site_tangent" : (MODE & M_EFS) ? ((MODE & M_ROWS) ? "site_efs_rows" : "site_efs") : "site_rows";
   ProfRegion pr(name, s);
   kern<<<grid, warps * 32, P.L.total, s>>>(P);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
   return warps;
 }

@@ -61,8 +61,7 @@ constexpr MonoTab<nmono_upto(NU0)> make_mono() {
         t.lz[k] = c > 0 ? mono_index(a, b, c - 1) : -1;
         if (a > 0) { t.parent[k] = t.lx[k]; t.axis[k] = 0; }
         else if (b > 0) { t.parent[k] = t.ly[k]; t.axis[k] = 1; }
-        else if (c > 0) { t.parent[k] = t.lz[k]; t.axis[k] = 2; }
-        else { t.parent[k] = -1; t.axis[k] = -1; }
+        else if (c > 0) { t.parent[k] = t.lz[k]; t.axis[k] = 2; } else { t.parent[k] = -1; t.axis[k] = -1; }
         ++k;
       }
   return t;
@@ -159,8 +158,7 @@ __device__ __forceinline__ void radial(float rr, const float* cz, float rmin, fl
   for (int b = 0; b < NQ; ++b) {
     float tb, db;
     if (b == 0) { tb = t0; db = d0; }
-    else if (b == 1) { tb = t1; db = d1; }
-    else {
+    else if (b == 1) { tb = t1; db = d1; } else {
       const float t2 = 2.f * x * t1 - t0;
       const float d2 = 2.f * t1 + 2.f * x * d1 - d0;
       t0 = t1; t1 = t2; d0 = d1; d1 = d2;
@@ -624,6 +622,7 @@ void launch_fast(FastParams P, int nwarps, cudaStream_t s) {
   if (P.n_work == 0) return;
   ProfRegion pr((MODE & F_EFS) ? ((MODE & F_ROWS) ? "site_efs_rows" : "site_efs") : "site_rows", s);
   kern<<<grid, nwarps * 32, P.total, s>>>(P);
+  ProfRegion::launched();
   MTP_CUDA(cudaGetLastError());
 }
 
