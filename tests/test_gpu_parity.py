@@ -218,6 +218,33 @@ def test_grade_random_active_set(api, prec):
         assert np.all(np.abs(g - gamma) <= 1e-4 * np.maximum(1.0, gamma))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grade_ternary_batch_every_atom(api, prec):
+    """Every atom of a ~250-atom ternary batch: the mixed path stores the rows in species order
+    and each 128-row tile skips the K chunks of species it does not hold (here tiles holding
+    species {0, 1} and {1, 2}, and the padding chunks past m = 383)."""
+    cfgs = [small_cfg(1, "fcc", 2, 3), small_cfg(2, "bcc", (2, 2, 3), 3), small_cfg(3, "hcp", (2, 2, 2), 3),
+            small_cfg(4, "fcc", (1, 1, 2), 3), small_cfg(5, "bcc", 3, 3), small_cfg(6, "fcc", 3, 3)]
+    bnp = synth.concat(cfgs)
+    assert len(bnp["type"]) > 128 and len(set(bnp["type"].tolist())) == 3
+    md = O.OracleModel(3, 16, 2.0, 5.0)
+    theta = theta_for(md, 31)
+    A = synth.diag_dominant(32, md.m)
+    model = api.mtp_load(api.make_desc(3, 16), theta)
+    b = api.Batch(bnp)
+    nb = api.mtp_build_neighbors(model, b)
+    api.mtp_set_active_set(model, torch.tensor(A, device="cuda"))
+    out = api.mtp_grade(model, b, nb, prec, threshold=np.inf)
+    rows = O.site_rows(md, theta, bnp["type"], O.batch_neighbors(bnp, 5.0))
+    gamma, am = O.grade(A, rows)
+    g = out["gamma"].cpu().numpy()
+    if prec == "fp64":
+        np.testing.assert_allclose(g, gamma, rtol=FP64_TOL)
+        assert (out["argmax"].cpu().numpy() == am).all()
+    else:
+        assert np.all(np.abs(g - gamma) <= 1e-4 * np.maximum(1.0, gamma))
+
+
 def test_grade_is_one_on_active_set_and_flags(api):
     bnp = synth.fcc_unary_108(sigma=0.25)
     md = O.OracleModel(1, 8, 2.0, 5.0)
