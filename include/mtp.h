@@ -41,7 +41,8 @@ typedef enum {
   MTP_ERR_SINGULAR = 4,    /* active-set matrix singular (LU pivot below tolerance) */
   MTP_ERR_GEOMETRY = 5,    /* coincident atoms (|r_ij| < 1e-8 A) or a degenerate cell */
   MTP_ERR_NUMERIC = 6,     /* non-finite input */
-  MTP_ERR_UNSUPPORTED = 7  /* request outside what this build supports */
+  MTP_ERR_UNSUPPORTED = 7, /* request outside what this build supports */
+  MTP_ERR_TIMEOUT = 8      /* a bounded wait inside a kernel expired (reported by mtp_sync) */
 } mtp_status;
 
 typedef enum { MTP_FP64 = 0, MTP_MIXED = 1 } mtp_precision;
@@ -172,16 +173,29 @@ mtp_status mtp_energy_forces_stress(mtp_model* model, const mtp_batch* batch, co
                                     mtp_precision prec, double* energy, double* site_energy,
                                     double* forces, double* virial, void* stream);
 
+/* mtp_energy_forces_stress plus the per-atom virials (DEVICE site_virial[N x 9], or NULL):
+ * W_i[a][b] = -sum_j (dV_i/dr_ij)_a (r_ij)_b, the site-based split of the virial (per-atom
+ * stress times volume); sum_{i in k} W_i = virial[k].  The split is a convention (not unique); this one
+ * charges each neighborhood's derivative to its center. */
+mtp_status mtp_energy_forces_stress_atoms(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
+                                          mtp_precision prec, double* energy, double* site_energy,
+                                          double* forces, double* virial, double* site_virial, void* stream);
+
 /* Allocation-free variant of mtp_energy_forces_stress (the paper has no counterpart).
  * For callers that may not allocate device memory at call time (an engine that owns the whole
  * device-memory budget through its own allocator, or a time-step loop that cannot afford an
  * allocation's synchronisation or failure).  Same arguments, outputs and precision as
- * mtp_energy_forces_stress; the scratch lives in a fixed 16 MiB device array inside the
- * library, held by every GPU that loads it until exit.  Limits: at most 32768 atoms, 524288
- * pairs and 1024 configuration segments (4096-atom pieces of the configurations), else
- * MTP_ERR_CAPACITY.  Calls no cudaMalloc/cudaFree.  The first call on a device looks up the
- * array's address, so make it before any stream capture.  Calls share the array: calls that
- * overlap on the GPU race and must be serialised by the caller. */
+ * mtp_energy_forces_stress (NULL outputs allowed likewise); the scratch lives in a fixed 16 MiB
+ * device array inside the library.  That array is committed on a device when the library's
+ * module is loaded there, which mtp_load does (so it is taken when a model is created, before
+ * a caller's pool grabs the rest of the memory), and it is held until the process exits.
+ * Limits: at most 32768 atoms, 524288 pairs and 1024 configuration segments (4096-atom pieces
+ * of the configurations), else MTP_ERR_CAPACITY.  Calls no cudaMalloc/cudaFree.  The CUDA
+ * runtime still loads each kernel's code on its first launch (lazy loading) unless
+ * CUDA_MODULE_LOADING=EAGER; one call of mtp_energy_forces_stress at start-up loads the same
+ * kernels.  A device reset invalidates every model (their device memory is gone); a model
+ * loaded afterwards looks the array up again.  Calls share the array: calls that overlap on the
+ * GPU race and must be serialised by the caller. */
 mtp_status mtp_energy_forces_stress_noalloc(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
                                             mtp_precision prec, double* energy, double* site_energy,
                                             double* forces, double* virial, void* stream);
@@ -227,6 +241,15 @@ mtp_status mtp_maxvol(mtp_model* model, const double* B, int64_t n, double eps, 
  * rows[n_cfg x m] FP64 out (sums over a configuration's atoms in a fixed order). */
 mtp_status mtp_config_rows(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
                            mtp_precision prec, double* rows, void* stream);
+
+/* Vector-Jacobian product of the configuration energies E_k (eq. 1) for reverse-mode
+ * differentiation: given DEVICE gE[n_cfg] (dL/dE_k),
+ *   g_theta[m] = sum_k gE_k dE_k/dtheta = sum_k gE_k sum_{i in k} b_i   (b_i of eq. 9; DEVICE, or NULL)
+ *   g_pos[N x 3] = dL/dx_i = -gE_{k(i)} F_i                               (DEVICE, or NULL)
+ * with F the forces of the forward pass (DEVICE forces[N x 3], required when g_pos is given).
+ * Sums run in a fixed order (deterministic).  Synchronises `stream`. */
+mtp_status mtp_energy_vjp(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr, mtp_precision prec,
+                          const double* gE, const double* forces, double* g_pos, double* g_theta, void* stream);
 
 typedef enum {
   MTP_GRADE_NEIGHBORHOOD = 0,   /* gamma(cfg) = max over the configuration's atoms of gamma_i */
@@ -284,12 +307,14 @@ mtp_status mtp_fit_bfgs(mtp_model* model, const mtp_batch* batch, const mtp_nbr*
 /* Autotuner for the per-neighborhood kernel's launch shape (the paper has no counterpart):
  * times the pass that mtp_step makes (energies, forces, virial, and the grade when an active
  * set is loaded) on this batch at every feasible number of warps per block (1..8 for the
- * specialised mixed kernel, 1, 2, 4 for the generic kernel; blocks per SM then follow from
- * the occupancy) and, for the level-20 shape of the mixed kernel, with the forward part of the
- * contraction schedule in shared or in global memory; keeps the fastest in the model for later
- * calls of this precision's kernel,
- * and returns it (HOST warps, HOST ms = its best time of three) -- either may be NULL.
- * Synchronises `stream`. */
+ * specialised single-kernel mixed pass, 1, 2, 4 for the generic kernel; blocks per SM then
+ * follow from the occupancy) and, for the level-20 shape of the single kernel, with the
+ * forward part of the contraction schedule in shared or in global memory; for the mixed path
+ * also the three-kernel pass (4 or 8 warps per block, 1 or 2 neighborhoods per contraction
+ * warp) unless mtp_set_mixed_pass fixed the single kernel.  Keeps the fastest in the model for
+ * later calls of this precision (with mixed pass 0, also which pass), and returns the single
+ * kernel's warps (HOST warps) and the best time of three of the chosen shape (HOST ms) --
+ * either may be NULL.  Synchronises `stream`. */
 mtp_status mtp_autotune(mtp_model* model, const mtp_batch* batch, const mtp_nbr* nbr,
                         mtp_precision prec, int32_t* warps, double* ms, void* stream);
 
@@ -299,6 +324,22 @@ mtp_status mtp_autotune(mtp_model* model, const mtp_batch* batch, const mtp_nbr*
  * warps_generic = warps per block of the generic kernel (0: untuned).  No GPU work. */
 mtp_status mtp_get_launch_shape(const mtp_model* model, int32_t* warps_fast, int32_t* fwd_global,
                                 int32_t* warps_generic);
+
+/* Which pass the mixed path runs (no counterpart in the paper; both compute the same method):
+ * 1 = one kernel per neighborhood (moments, contraction, adjoint and rows in one pass, the
+ * allocation-free entry point's kernel), 2 = three kernels (moments; contraction and its
+ * adjoint; pair adjoint), with the moments and their adjoints in a library workspace of
+ * 4 ceil4(n_moment_components) bytes per atom; 0 = automatic: the three kernels where the
+ * model's shape has them, unless mtp_autotune found the single kernel faster.  Results of the
+ * two passes agree to FP32 rounding; each pass is bitwise reproducible under every launch shape.
+ * MTP_ERR_UNSUPPORTED for 2 when the shape has no three-kernel pass.  No GPU work. */
+mtp_status mtp_set_mixed_pass(mtp_model* model, int pass);
+
+/* The setting above, the pass the next mixed call will run (1 or 2), and the three-kernel
+ * pass's tuned shape (warps per block of its per-pair kernels, neighborhoods per warp of its
+ * contraction; 0 = default).  HOST outputs, any may be NULL. */
+mtp_status mtp_get_mixed_pass(const mtp_model* model, int32_t* setting, int32_t* in_use, int32_t* split_warps,
+                              int32_t* split_nb);
 
 /* Checkpoint (the paper keeps theta, the active set and its mode in its .almtp file): the
  * model's descriptor, theta and, if loaded, the active-set matrix A, in a HOST byte buffer
@@ -313,9 +354,19 @@ mtp_status mtp_restore(const void* buffer, int64_t size, mtp_model** model, void
  * MTP_FAULT_DEVICE_ALLOC makes the next `count` growths of a library workspace fail as a device
  * allocation failure (MTP_ERR_CUDA); MTP_FAULT_NEIGHBOR_OVERFLOW flags the next `count`
  * neighbor fills as overflowing their counted capacity (the build repeats a failed fill once,
- * then returns MTP_ERR_CAPACITY).  count = 0 disarms.  Process-wide. */
-enum { MTP_FAULT_DEVICE_ALLOC = 1, MTP_FAULT_NEIGHBOR_OVERFLOW = 2 };
+ * then returns MTP_ERR_CAPACITY); MTP_FAULT_GRADE_WAIT gives every wait of the next `count`
+ * tensor-core grade launches a single try, so the first wait not already satisfied expires and
+ * the kernel takes its abort path (stops, drains its own copies and MMAs with the default
+ * bound, frees tensor memory, leaves the unfinished gamma NaN; mtp_sync then returns
+ * MTP_ERR_TIMEOUT).  count = 0 disarms.  Process-wide. */
+enum { MTP_FAULT_DEVICE_ALLOC = 1, MTP_FAULT_NEIGHBOR_OVERFLOW = 2, MTP_FAULT_GRADE_WAIT = 3 };
 mtp_status mtp_debug_inject(int fault, int count);
+
+/* Synchronise `stream` and report errors that asynchronous kernels of this model latched on
+ * the device since the last mtp_sync (mtp_grade and mtp_step return before their kernels run):
+ * MTP_ERR_TIMEOUT if a bounded wait of the tensor-core grade expired (the gamma_i it did not
+ * finish are NaN).  Clears the latch. */
+mtp_status mtp_sync(mtp_model* model, void* stream);
 
 /* Current parameter vector theta (HOST out, m FP64). */
 mtp_status mtp_get_params(const mtp_model* model, double* theta, int64_t m);
@@ -350,6 +401,14 @@ mtp_status mtp_train_step(mtp_model* model, const mtp_batch* batch, const mtp_nb
                           mtp_precision prec, const double* E_ref, const double* F_ref,
                           const double* W_ref, double w_e, double w_f, double w_s, double* loss,
                           double* grad, void* stream);
+
+/* Arithmetic peak of the current GPU by the library's own microbenchmark (no counterpart in
+ * the paper; the denominators of the kernels' roofline fractions): kind 0 = FP32 FMA, 1 = FP64
+ * FMA (8 independent FMA chains per thread, full occupancy), 2 = TF32 tensor-core MMA
+ * (tcgen05.mma.kind::tf32, M 128, N 256, K 8, one issuing thread per SM, operands fixed in
+ * shared memory).  HOST out tflops (2 flops per multiply-add) and ms (best of three timed runs
+ * after one warm-up, CUDA events on `stream`).  Synchronises `stream`. */
+mtp_status mtp_measure_peak(int kind, double* tflops, double* ms, void* stream);
 
 /* ---------------------------------------------------------------------------------- */
 /* Tracing (no counterpart in the paper)                                              */

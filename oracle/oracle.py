@@ -63,6 +63,16 @@ def _p(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
+def threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(_lib().omp_get_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Set the OpenMP thread count of the oracle's parallel loops (process-wide)."""
+    _lib().omp_set_num_threads(int(n))
+
+
 @dataclass
 class OracleModel:
     n_types: int

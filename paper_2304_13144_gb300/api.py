@@ -21,7 +21,7 @@ MTP_MIXED = 1
 MTP_GRADE_NEIGHBORHOOD = 0
 MTP_GRADE_CONFIGURATION = 1
 STATUS = {0: "MTP_OK", 1: "MTP_ERR_ARG", 2: "MTP_ERR_CUDA", 3: "MTP_ERR_CAPACITY", 4: "MTP_ERR_SINGULAR",
-          5: "MTP_ERR_GEOMETRY", 6: "MTP_ERR_NUMERIC", 7: "MTP_ERR_UNSUPPORTED"}
+          5: "MTP_ERR_GEOMETRY", 6: "MTP_ERR_NUMERIC", 7: "MTP_ERR_UNSUPPORTED", 8: "MTP_ERR_TIMEOUT"}
 
 
 class MtpError(RuntimeError):
@@ -69,12 +69,17 @@ _SIGS = {
     "mtp_save": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
     "mtp_restore": (ctypes.c_int, [_P, _I64, _P, _P]),
     "mtp_debug_inject": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "mtp_sync": (ctypes.c_int, [_P, _P]),
+    "mtp_set_mixed_pass": (ctypes.c_int, [_P, ctypes.c_int]),
+    "mtp_get_mixed_pass": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "mtp_measure_peak": (ctypes.c_int, [ctypes.c_int, _P, _P, _P]),
     "mtp_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "mtp_fit_bfgs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _I64, _D, _P, _P, _P]),
     "mtp_fit_errors": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "mtp_get_params": (ctypes.c_int, [_P, _P, _I64]),
     "mtp_cut_clusters": (ctypes.c_int, [_P, _P, _I64, _D, _P, _P, _P, _P, _I64, _P, _P]),
     "mtp_config_rows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
+    "mtp_energy_vjp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "mtp_config_grade": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, _D, _D, _P, _P, _P, _P]),
     "mtp_maxvol": (ctypes.c_int, [_P, _P, _I64, _D, _I64, _P, _P, _P]),
     "mtp_build_neighbors": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -82,6 +87,7 @@ _SIGS = {
     "mtp_nbr_size": (ctypes.c_int, [_P, _P, _P]),
     "mtp_nbr_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "mtp_energy_forces_stress": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "mtp_energy_forces_stress_atoms": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "mtp_energy_forces_stress_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "mtp_param_rows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _I64, _P, _P]),
     "mtp_grade": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _D, _P, _P, _P, _P, _P]),
@@ -338,14 +344,29 @@ def mtp_energy_forces_stress(model, batch, nbr, prec="mixed", energy=None, site_
     return {"energy": energy, "site_energy": site_energy, "forces": forces, "virial": virial}
 
 
-def mtp_energy_forces_stress_noalloc(model, batch, nbr, prec="mixed", stream=None):
-    """Allocation-free energies/forces/virial: the library allocates nothing (outputs are
-    allocated here by torch, before the call)."""
+def mtp_energy_forces_stress_atoms(model, batch, nbr, prec="mixed", stream=None):
+    """Energies, site energies, forces, virial and per-atom virials W_i (N, 3, 3)."""
     N, K = batch.n_atoms, batch.n_cfg
-    energy = torch.empty(K, dtype=torch.float64, device="cuda")
-    site_energy = torch.empty(N, dtype=torch.float64, device="cuda")
-    forces = torch.empty((N, 3), dtype=torch.float64, device="cuda")
-    virial = torch.empty((K, 3, 3), dtype=torch.float64, device="cuda")
+    out = {"energy": torch.empty(K, dtype=torch.float64, device="cuda"),
+           "site_energy": torch.empty(N, dtype=torch.float64, device="cuda"),
+           "forces": torch.empty((N, 3), dtype=torch.float64, device="cuda"),
+           "virial": torch.empty((K, 3, 3), dtype=torch.float64, device="cuda"),
+           "site_virial": torch.empty((N, 3, 3), dtype=torch.float64, device="cuda")}
+    _check(lib().mtp_energy_forces_stress_atoms(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec),
+                                                *[_ptr(out[k]) for k in ("energy", "site_energy", "forces", "virial",
+                                                                        "site_virial")], _stream(stream)))
+    return out
+
+
+def mtp_energy_forces_stress_noalloc(model, batch, nbr, prec="mixed",
+                                     want=("energy", "forces", "virial", "site_energy"), stream=None):
+    """Allocation-free energies/forces/virial: the library allocates nothing (the requested
+    outputs are allocated here by torch, before the call; the others are passed as NULL)."""
+    N, K = batch.n_atoms, batch.n_cfg
+    energy = torch.empty(K, dtype=torch.float64, device="cuda") if "energy" in want else None
+    site_energy = torch.empty(N, dtype=torch.float64, device="cuda") if "site_energy" in want else None
+    forces = torch.empty((N, 3), dtype=torch.float64, device="cuda") if "forces" in want else None
+    virial = torch.empty((K, 3, 3), dtype=torch.float64, device="cuda") if "virial" in want else None
     _check(lib().mtp_energy_forces_stress_noalloc(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(energy),
                                                   _ptr(site_energy), _ptr(forces), _ptr(virial), _stream(stream)))
     return {"energy": energy, "site_energy": site_energy, "forces": forces, "virial": virial}
@@ -396,6 +417,18 @@ def mtp_config_rows(model, batch, nbr, prec="fp64", stream=None):
     rows = torch.empty((batch.n_cfg, model.n_params), dtype=torch.float64, device="cuda")
     _check(lib().mtp_config_rows(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(rows), _stream(stream)))
     return rows
+
+
+def mtp_energy_vjp(model, batch, nbr, gE, forces=None, want_pos=True, want_theta=True, prec="fp64", stream=None):
+    """(g_pos, g_theta): the vector-Jacobian product of the configuration energies for the
+    cotangent gE (n_cfg,); either output is None when not requested."""
+    gE = gE.to(device="cuda", dtype=torch.float64).contiguous()
+    g_pos = torch.empty((batch.n_atoms, 3), dtype=torch.float64, device="cuda") if want_pos else None
+    g_theta = torch.empty(model.n_params, dtype=torch.float64, device="cuda") if want_theta else None
+    F = forces.contiguous() if forces is not None else None
+    _check(lib().mtp_energy_vjp(model.h, ctypes.byref(batch.c), nbr.h, _prec(prec), _ptr(gE), _ptr(F), _ptr(g_pos),
+                                _ptr(g_theta), _stream(stream)))
+    return g_pos, g_theta
 
 
 def mtp_config_grade(model, batch, nbr, prec="fp64", mode="neighborhood", gamma_save=2.0, gamma_break=10.0,
@@ -473,6 +506,19 @@ def mtp_autotune(model, batch, nbr, prec="mixed", stream=None):
     return w.value, ms.value
 
 
+def mtp_set_mixed_pass(model, p):
+    """0 automatic, 1 single kernel, 2 three kernels (or the names "auto", "single", "split")."""
+    p = {"auto": 0, "single": 1, "split": 2}.get(p, p)
+    _check(lib().mtp_set_mixed_pass(model.h, int(p)))
+
+
+def mtp_get_mixed_pass(model):
+    """(setting, pass in use: 1 or 2, split warps, split neighborhoods per warp)."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().mtp_get_mixed_pass(model.h, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
 def mtp_get_launch_shape(model):
     """The autotuner's shapes kept in the model: (warps_fast, fwd_global, warps_generic)."""
     a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -503,11 +549,25 @@ def mtp_restore(blob: bytes, stream=None) -> Model:
 
 MTP_FAULT_DEVICE_ALLOC = 1
 MTP_FAULT_NEIGHBOR_OVERFLOW = 2
+MTP_FAULT_GRADE_WAIT = 3
 
 
 def mtp_debug_inject(fault, count):
     """Arm a host-side fault for the next `count` events (0 disarms)."""
     _check(lib().mtp_debug_inject(int(fault), int(count)))
+
+
+def mtp_sync(model, stream=None):
+    """Synchronise the stream; raise the device-side error latched by earlier asynchronous calls."""
+    _check(lib().mtp_sync(model.h, _stream(stream)))
+
+
+def mtp_measure_peak(kind, stream=None):
+    """(TFLOP/s, ms) of the library's microbenchmark: kind "fp32_fma", "fp64_fma" or "tf32_mma"."""
+    k = {"fp32_fma": 0, "fp64_fma": 1, "tf32_mma": 2}[kind]
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mtp_measure_peak(k, ctypes.byref(tf), ctypes.byref(ms), _stream(stream)))
+    return tf.value, ms.value
 
 
 def mtp_get_params(model):

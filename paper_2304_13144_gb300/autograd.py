@@ -1,10 +1,11 @@
 """torch.autograd.Function wrappers around the C ABI (argument marshalling only).
 
 * ``MTPEnergy``: per-configuration energies E_k (eq. 1) as a function of the atomic
-  positions and of the parameter vector theta.  Its backward pass uses the hand-written
-  adjoint kernels: dE_k/dx_i = -F_i for atoms i of configuration k (forces from the same
-  call as the energies), and dE_k/dtheta = sum_{i in k} b_i with b_i = dV_i/dtheta (eq. 9)
-  from mtp_param_rows.
+  positions and of the parameter vector theta.  Its backward pass is one library call,
+  mtp_energy_vjp, on the hand-written adjoint kernels: dE_k/dx_i = -F_i for atoms i of
+  configuration k (forces from the same call as the energies), and
+  dE_k/dtheta = sum_{i in k} b_i with b_i = dV_i/dtheta (eq. 9), contracted with the cotangent
+  in the library.
 * ``MTPLoss``: the energy/force/stress loss of eq. 7 as a function of theta; its backward
   returns the gradient that mtp_train_step computes (second hand-written kernel).
 
@@ -21,11 +22,6 @@ from . import api
 
 def _set_theta(model, theta: torch.Tensor):
     api.mtp_set_params(model, theta.detach().to("cpu", torch.float64).numpy())
-
-
-def _config_of_atom(batch) -> torch.Tensor:
-    counts = batch.atom_offset[1:] - batch.atom_offset[:-1]
-    return torch.repeat_interleave(torch.arange(batch.n_cfg, device=counts.device), counts)
 
 
 class MTPEnergy(torch.autograd.Function):
@@ -53,14 +49,10 @@ class MTPEnergy(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gE):
         (F,) = ctx.saved_tensors
-        gE = gE.to(device=F.device, dtype=torch.float64)
-        g_pos = g_theta = None
-        cfg = _config_of_atom(ctx.batch)
-        if ctx.needs_input_grad[0]:
-            g_pos = -F * gE[cfg][:, None]
-        if ctx.needs_input_grad[1]:
-            rows = api.mtp_param_rows(ctx.model, ctx.batch, ctx.nbr, ctx.prec)
-            g_theta = (gE[cfg][:, None] * rows).sum(dim=0).to(ctx.theta_device)
+        g_pos, g_theta = api.mtp_energy_vjp(ctx.model, ctx.batch, ctx.nbr, gE, F, want_pos=ctx.needs_input_grad[0],
+                                            want_theta=ctx.needs_input_grad[1], prec=ctx.prec)
+        if g_theta is not None:
+            g_theta = g_theta.to(ctx.theta_device)
         return g_pos, g_theta, None, None, None
 
 

@@ -19,6 +19,8 @@ LIB = os.path.join(OUT, "libmtp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fno-strict-aliasing"]
+# MTP_DEFINES="MTP_SPLIT_CHECK ..." adds -D flags (range-checked builds of selected kernels)
+NVCC_FLAGS += [f"-D{x}" for x in os.environ.get("MTP_DEFINES", "").split() if x]
 
 
 def _nvcc() -> str:

@@ -7,8 +7,8 @@ shapes and sizes of the benchmark configurations:
   C3  512 training configurations of 8-256 atoms, level-16 ternary student
   C4  fcc ternary random solid solution 64^3 cells (1,048,576 atoms), level 20 (benchmark)
   C5  liquid-like quaternary, 2,097,152 atoms, R_cut 6 A, level 24
-`workload(name).inputs()` returns the batch dict (see synth.py), `.desc()` the model
-descriptor and `.theta()` the seeded parameter vector.
+`workload(name).inputs(seed)` returns the batch dict (see synth.py; seed None = the workload's
+own structure seed), `.desc()` the model descriptor and `.theta()` the seeded parameter vector.
 """
 from __future__ import annotations
 
@@ -26,12 +26,13 @@ class Workload:
     r_cut: float
     theta_seed: int
     nbar: float                      # mean neighbor count for the parameter scale (reading R14)
-    make_inputs: Callable[[], dict] = field(repr=False)
+    input_seed: int
+    make_inputs: Callable[[int], dict] = field(repr=False)
     r_min: float = 2.0
     n_q: int = 8
 
-    def inputs(self) -> dict:
-        return self.make_inputs()
+    def inputs(self, seed: int | None = None) -> dict:
+        return self.make_inputs(self.input_seed if seed is None else seed)
 
     def desc(self):
         from . import api
@@ -49,12 +50,12 @@ class Workload:
 
 
 WORKLOADS = {
-    "C1": Workload("fcc unary 108 atoms", 1, 8, 5.0, 11, 42.0, lambda: synth.fcc_unary_108(seed=1)),
-    "C2": Workload("B2 binary 40^3 cells", 2, 16, 5.0, 22, 58.0, lambda: synth.b2_binary(seed=2, n=40)),
-    "C3": Workload("512 training configurations", 3, 16, 5.0, 34, 42.0, lambda: synth.training_batch(seed=3)),
-    "C4": Workload("fcc ternary 64^3 cells", 3, 20, 5.0, 44, 42.0, lambda: synth.fcc_ternary(seed=4, n=64)),
-    "C5": Workload("liquid quaternary 2,097,152 atoms", 4, 24, 6.0, 55, 76.0,
-                   lambda: synth.liquid_rsa(seed=5, tiles=4)),
+    "C1": Workload("fcc unary 108 atoms", 1, 8, 5.0, 11, 42.0, 1, lambda s: synth.fcc_unary_108(seed=s)),
+    "C2": Workload("B2 binary 40^3 cells", 2, 16, 5.0, 22, 58.0, 2, lambda s: synth.b2_binary(seed=s, n=40)),
+    "C3": Workload("512 training configurations", 3, 16, 5.0, 34, 42.0, 3, lambda s: synth.training_batch(seed=s)),
+    "C4": Workload("fcc ternary 64^3 cells", 3, 20, 5.0, 44, 42.0, 4, lambda s: synth.fcc_ternary(seed=s, n=64)),
+    "C5": Workload("liquid quaternary 2,097,152 atoms", 4, 24, 6.0, 55, 76.0, 5,
+                   lambda s: synth.liquid_rsa(seed=s, tiles=4)),
 }
 
 

@@ -19,6 +19,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 
 std::atomic<int> g_inject_alloc{0};
 std::atomic<int> g_inject_overflow{0};
+std::atomic<int> g_inject_grade_wait{0};
 
 bool take_injected(std::atomic<int>& c) {
   int v = c.load();
@@ -425,21 +426,15 @@ void check_model(const mtp_model* m) {
   if (dev != m->device) throw Fail{MTP_ERR_ARG, "model belongs to another device"};
 }
 
-void check_run(const mtp_model* m, const mtp_batch* b, const mtp_nbr* nb) {
-  check_model(m);
-  if (!b || !nb) throw Fail{MTP_ERR_ARG, "null batch or neighbor list"};
-  if (b->n_cfg != nb->n_cfg) throw Fail{MTP_ERR_ARG, "neighbor list was built for another batch"};
-  if (!b->pos || !b->type || !b->cell) throw Fail{MTP_ERR_ARG, "batch: null array"};
-}
-
 // Shared body of the EFS / grade / step entry points.
 void efs_and_grade(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec, double* energy,
                    double* site_energy, double* forces, double* virial, double threshold, double* gamma,
-                   int32_t* argmax, int32_t* flagged, int64_t* n_flagged, cudaStream_t s) {
+                   int32_t* argmax, int32_t* flagged, int64_t* n_flagged, cudaStream_t s,
+                   double* site_virial = nullptr) {
   check_run(m, b, nb);
   if (prec != MTP_FP64 && prec != MTP_MIXED) throw Fail{MTP_ERR_ARG, "unknown precision"};
   const bool fp64 = prec == MTP_FP64;
-  const bool want_efs = energy || site_energy || forces || virial;
+  const bool want_efs = energy || site_energy || forces || virial || site_virial;
   const bool want_grade = gamma != nullptr;
   if (!want_efs && !want_grade) throw Fail{MTP_ERR_ARG, "no output requested"};
   if ((flagged || n_flagged) && !gamma) throw Fail{MTP_ERR_ARG, "flagging needs gamma"};
@@ -451,8 +446,12 @@ void efs_and_grade(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, mtp_prec
     m->ws_pair.ensure(std::max<int64_t>(P, 1) * 3 * rsz, s);
     m->ws_atom.ensure(N * 10 * sizeof(double), s);
     o.V = site_energy ? site_energy : m->ws_atom.as<double>();
-    o.Wat = m->ws_atom.as<double>() + N;
+    o.Wat = site_virial ? site_virial : m->ws_atom.as<double>() + N;
     o.G = m->ws_pair.p;
+  }
+  if (!fp64 && split_wanted(m)) {
+    m->ws_mom.ensure(std::max<int64_t>(N, 1) * split_ldm(m->ds.n_mom) * sizeof(float), s);
+    o.mom = m->ws_mom.as<float>();
   }
   int64_t ld = 0;
   const bool use_tc = !fp64 && want_grade && grade_tc_available(m);
@@ -509,6 +508,15 @@ void efs_and_grade(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, mtp_prec
 }
 
 }  // namespace
+
+namespace mtp {
+void check_run(const mtp_model* m, const mtp_batch* b, const mtp_nbr* nb) {
+  check_model(m);
+  if (!b || !nb) throw Fail{MTP_ERR_ARG, "null batch or neighbor list"};
+  if (b->n_cfg != nb->n_cfg) throw Fail{MTP_ERR_ARG, "neighbor list was built for another batch"};
+  if (!b->pos || !b->type || !b->cell) throw Fail{MTP_ERR_ARG, "batch: null array"};
+}
+}  // namespace mtp
 
 extern "C" {
 
@@ -582,6 +590,10 @@ mtp_status mtp_load(const mtp_desc* desc, const double* theta, int64_t m, mtp_mo
       md->theta.assign(theta, theta + m);
       upload_schedule(md);
       upload_theta(md);
+      split_prepare(md);
+      noalloc_prepare(md->device);
+      md->async_err.ensure(sizeof(unsigned), 0);
+      MTP_CUDA(cudaMemset(md->async_err.p, 0, sizeof(unsigned)));
       MTP_CUDA(cudaDeviceSynchronize());
     } catch (...) {
       mtp_free_model(md);
@@ -599,7 +611,7 @@ void mtp_free_model(mtp_model* md) {
   cudaDeviceSynchronize();
   for (DevBuf* b : {&md->sched_buf, &md->theta_buf, &md->a_d, &md->ainv_d, &md->ainv_f, &md->ws_pair,
                     &md->ws_atom, &md->ws_rows, &md->ws_grade, &md->ws_sort, &md->ws_misc, &md->ws_red,
-                    &md->err_flag})
+                    &md->err_flag, &md->async_err, &md->split_tab, &md->ws_mom})
     b->release();
   cudaSetDevice(cur);
   delete md;
@@ -662,6 +674,9 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     MTP_CUDA(cudaEventCreate(&e1));
     int best_w = 0, best_p = -1;
     float best_ms = 0.f;
+    const int keep_pass = md->mixed_pass;
+    if (fast && keep_pass != 2) md->mixed_pass = 1;   // the single-kernel shapes first
+    struct Restore { mtp_model* m; int v; ~Restore() { m->mixed_pass = v; } } restore{md, keep_pass};
     // candidate shapes: (forward-slab placement, warps per block); the generic kernel has only warps
     for (int place = 0; place < (fast ? 2 : 1); ++place) {
       if (fast) md->tune_fwd_global = place;
@@ -685,10 +700,45 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
         if (best_w == 0 || t_min < best_ms) { best_ms = t_min; best_w = md->last_warps; best_p = place; }
       }
     }
+    // the three-kernel mixed pass, when the model has one: warps per block of its per-pair
+    // kernels x neighborhoods per warp of its contraction (results are the same for every shape)
+    int best_sw = 0, best_snb = 0;
+    float best_split = 0.f;
+    const int keep_split = md->tune_split;
+    md->mixed_pass = keep_pass;
+    if (fast && md->split_tab.p && keep_pass != 1) {
+      md->tune_split = 1;
+      for (int sw : {4, 8})
+        for (int snb : {1, 2}) {
+          md->tune_split_warps = sw;
+          md->tune_split_nb = snb;
+          run();
+          if (!md->last_split) continue;
+          float t_min = 0.f;
+          for (int rep = 0; rep < 3; ++rep) {
+            MTP_CUDA(cudaEventRecord(e0, s));
+            run();
+            MTP_CUDA(cudaEventRecord(e1, s));
+            MTP_CUDA(cudaEventSynchronize(e1));
+            float t = 0.f;
+            MTP_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            if (rep == 0 || t < t_min) t_min = t;
+          }
+          if (best_sw == 0 || t_min < best_split) { best_split = t_min; best_sw = sw; best_snb = snb; }
+        }
+      md->tune_split = keep_split;
+    }
     MTP_CUDA(cudaEventDestroy(e0));
     MTP_CUDA(cudaEventDestroy(e1));
     knob = best_w;
     if (fast) md->tune_fwd_global = best_p;
+    if (best_sw > 0) {
+      md->tune_split_warps = best_sw;
+      md->tune_split_nb = best_snb;
+      const bool split = md->mixed_pass == 2 || best_split < best_ms;
+      if (md->mixed_pass == 0) md->tune_split = split ? 1 : 0;
+      if (split) best_ms = best_split;
+    }
     MTP_CUDA(cudaStreamSynchronize(s));
     if (warps) *warps = best_w;
     if (ms) *ms = best_ms;
@@ -702,6 +752,26 @@ mtp_status mtp_get_launch_shape(const mtp_model* md, int32_t* warps_fast, int32_
     if (warps_fast) *warps_fast = md->tune_warps_fast;
     if (fwd_global) *fwd_global = md->tune_fwd_global;
     if (warps_generic) *warps_generic = md->tune_warps_generic;
+  });
+}
+
+mtp_status mtp_set_mixed_pass(mtp_model* md, int pass) {
+  return guarded([&] {
+    check_model(md);
+    if (pass < 0 || pass > 2) throw Fail{MTP_ERR_ARG, "pass must be 0 (automatic), 1 (single kernel) or 2 (three kernels)"};
+    if (pass == 2 && !md->split_tab.p) throw Fail{MTP_ERR_UNSUPPORTED, "no three-kernel pass for this model's shape"};
+    md->mixed_pass = pass;
+  });
+}
+
+mtp_status mtp_get_mixed_pass(const mtp_model* md, int32_t* setting, int32_t* in_use, int32_t* split_warps,
+                              int32_t* split_nb) {
+  return guarded([&] {
+    if (!md) throw Fail{MTP_ERR_ARG, "null model"};
+    if (setting) *setting = md->mixed_pass;
+    if (in_use) *in_use = split_wanted(md) ? 2 : 1;
+    if (split_warps) *split_warps = md->tune_split_warps;
+    if (split_nb) *split_nb = md->tune_split_nb;
   });
 }
 
@@ -796,7 +866,23 @@ mtp_status mtp_debug_inject(int fault, int count) {
     if (count < 0) throw Fail{MTP_ERR_ARG, "negative count"};
     if (fault == MTP_FAULT_DEVICE_ALLOC) g_inject_alloc = count;
     else if (fault == MTP_FAULT_NEIGHBOR_OVERFLOW) g_inject_overflow = count;
+    else if (fault == MTP_FAULT_GRADE_WAIT) g_inject_grade_wait = count;
     else throw Fail{MTP_ERR_ARG, "unknown fault"};
+  });
+}
+
+mtp_status mtp_sync(mtp_model* md, void* stream) {
+  return guarded([&] {
+    check_model(md);
+    cudaStream_t s = as_stream(stream);
+    unsigned flag = 0;
+    MTP_CUDA(cudaMemcpyAsync(&flag, md->async_err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MTP_CUDA(cudaStreamSynchronize(s));
+    if (flag) {
+      MTP_CUDA(cudaMemsetAsync(md->async_err.p, 0, sizeof(unsigned), s));
+      MTP_CUDA(cudaStreamSynchronize(s));
+      throw Fail{MTP_ERR_TIMEOUT, "a bounded wait of the tensor-core grade expired; the grades it did not finish are NaN"};
+    }
   });
 }
 
@@ -934,6 +1020,15 @@ mtp_status mtp_energy_forces_stress(mtp_model* md, const mtp_batch* b, const mtp
   });
 }
 
+mtp_status mtp_energy_forces_stress_atoms(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec,
+                                          double* energy, double* site_energy, double* forces, double* virial,
+                                          double* site_virial, void* stream) {
+  return guarded([&] {
+    efs_and_grade(md, b, nb, prec, energy, site_energy, forces, virial, 0.0, nullptr, nullptr, nullptr, nullptr,
+                  as_stream(stream), site_virial);
+  });
+}
+
 mtp_status mtp_grade(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec, double threshold,
                      double* gamma, int32_t* argmax, int32_t* flagged, int64_t* n_flagged, void* stream) {
   return guarded([&] {
@@ -957,6 +1052,32 @@ mtp_status mtp_config_rows(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb,
     o.rows_ld = m;
     run_sites(md, b, nb, prec == MTP_FP64, o, false, nullptr, s);
     run_config_row_sums(nb, md->ws_rows.as<double>(), m, rows, md->ws_red, s);
+  });
+}
+
+mtp_status mtp_energy_vjp(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mtp_precision prec,
+                          const double* gE, const double* forces, double* g_pos, double* g_theta, void* stream) {
+  return guarded([&] {
+    check_run(md, b, nb);
+    if (prec != MTP_FP64 && prec != MTP_MIXED) throw Fail{MTP_ERR_ARG, "unknown precision"};
+    if (!gE || (!g_pos && !g_theta)) throw Fail{MTP_ERR_ARG, "null gE or no output requested"};
+    if (g_pos && !forces) throw Fail{MTP_ERR_ARG, "g_pos needs the forces of the forward pass"};
+    cudaStream_t s = as_stream(stream);
+    const int64_t m = md->sched.n_params, N = nb->n_atoms, K = nb->n_cfg;
+    DevBuf work;
+    double* R = nullptr;
+    if (g_theta) {
+      work.ensure(std::max<int64_t>(K, 1) * m * sizeof(double), s);
+      R = work.as<double>();
+      md->ws_rows.ensure(std::max<int64_t>(N, 1) * m * sizeof(double), s);
+      SiteOutputs o;
+      o.rows = md->ws_rows.as<double>();
+      o.rows_ld = m;
+      run_sites(md, b, nb, prec == MTP_FP64, o, false, nullptr, s);
+      run_config_row_sums(nb, md->ws_rows.as<double>(), m, R, md->ws_red, s);
+    }
+    run_energy_vjp(nb, R, gE, m, forces, g_pos, g_theta, s);
+    MTP_CUDA(cudaStreamSynchronize(s));   // `work` is released on return
   });
 }
 

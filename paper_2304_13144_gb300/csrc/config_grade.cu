@@ -96,6 +96,24 @@ __global__ void k_classify(const double* gamma, int64_t n, double g_save, double
   cls[k] = (g > g_save ? 1 : 0) + (g > g_break ? 1 : 0);
 }
 
+// vector-Jacobian product of the configuration energies (eq. 1): dtheta[p] = sum_k gE[k] R[k][p]
+// with R the configuration rows, summed over k in order (deterministic)
+__global__ void k_vjp_theta(const double* R, const double* gE, int n_cfg, int64_t m, double* g) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= m) return;
+  double acc = 0.0;
+  for (int k = 0; k < n_cfg; ++k) acc = fma(gE[k], R[k * m + p], acc);
+  g[p] = acc;
+}
+
+// dE_k/dx_i = -F_i for the atoms i of configuration k, scaled by gE[k]
+__global__ void k_vjp_pos(const double* F, const double* gE, const int* atom_cfg, int64_t N, double* g) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= N) return;
+  const double w = gE[atom_cfg[i]];
+  for (int c = 0; c < 3; ++c) g[3 * i + c] = -w * F[3 * i + c];
+}
+
 __global__ void k_widen_argmax(const int32_t* in, int64_t n, int64_t* out) {
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (k < n) out[k] = in[k];
@@ -137,6 +155,20 @@ void run_classify(const double* gamma, int64_t n, double g_save, double g_break,
   if (n == 0) return;
   k_classify<<<blocks(n, 256), 256, 0, s>>>(gamma, n, g_save, g_break, cls);
   ProfRegion::launched();
+  MTP_CUDA(cudaGetLastError());
+}
+
+void run_energy_vjp(const mtp_nbr* nb, const double* R, const double* gE, int64_t m, const double* F, double* g_pos,
+                    double* g_theta, cudaStream_t s) {
+  ProfRegion pr("energy_vjp", s);
+  if (g_theta && m > 0) {
+    k_vjp_theta<<<blocks(m, 128), 128, 0, s>>>(R, gE, static_cast<int>(nb->n_cfg), m, g_theta);
+    ProfRegion::launched();
+  }
+  if (g_pos && nb->n_atoms > 0) {
+    k_vjp_pos<<<blocks(nb->n_atoms, 256), 256, 0, s>>>(F, gE, nb->dn.atom_cfg, nb->n_atoms, g_pos);
+    ProfRegion::launched();
+  }
   MTP_CUDA(cudaGetLastError());
 }
 

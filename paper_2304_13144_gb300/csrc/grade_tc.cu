@@ -11,8 +11,9 @@
 //   warp 1: allocates TMEM and issues tcgen05.mma (M = 128, N = 224, K = 8 per instruction),
 //   warps 2-5: epilogue, one row per thread (tcgen05.ld 32x32b), two TMEM accumulators so the
 //              epilogue of one 224-column pass overlaps the MMAs of the next.
-// Every mbarrier wait is bounded: on expiry the kernel records an error flag, stops issuing,
-// waits (bounded) for its own copies and MMAs in flight, frees TMEM and returns.
+// Every mbarrier wait is bounded (a.wait_limit tries): on expiry the kernel records an error in
+// the model's latch, stops issuing, waits for its own copies and MMAs in flight (bounded by the
+// default limit, whatever a.wait_limit is), frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -35,7 +36,7 @@ constexpr int B_BYTES = BN * BK * 4;   // 28 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int TMEM_COLS = 512;
 constexpr int THREADS = 192;
-constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;   // default tries per wait (>= 1 s with the back-off)
 constexpr size_t SMEM_BYTES = STAGES * STAGE_BYTES + 256 + 1024;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -65,9 +66,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; false = gave up (abort flag set by the caller)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+// bounded wait of at most `limit` tries; false = gave up (abort flag set by the caller)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint32_t limit = WAIT_LIMIT) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
     if (it > 64) __nanosleep(64);
@@ -131,7 +133,8 @@ struct TcArgs {
   int64_t n_work;      // n_tiles * n_pass work items (tile, pass)
   float* pbest;        // [n_pass x N] per-pass row maxima
   int32_t* parg;       // [n_pass x N] and their columns
-  unsigned* err;
+  unsigned* err;       // the model's asynchronous error latch (bit 1: a wait expired)
+  uint32_t wait_limit; // tries per wait in normal operation (the drain waits use WAIT_LIMIT)
   // rows grouped by the center's species (zrow[r], ascending) or zrow == null: the radial block
   // of b_i is zero outside the center's species, so a K chunk that lies in the blocks of species
   // absent from a tile (or in the padding past n_params) is skipped for that tile
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
           for (int kc = 0; kc < a.k_chunks; ++kc) {
             if (chunk_zero(a, kc, zlo, zhi)) continue;
             const uint32_t s = it % STAGES, n = it / STAGES;
-            if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag)) { *abort_flag = 1; break; }
+            if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag, a.wait_limit)) { *abort_flag = 1; break; }
             unsigned char* st = ring + s * STAGE_BYTES;
             mbar_expect_tx(&full[s], STAGE_BYTES);
             const int x = kc * BK, yr = static_cast<int>(tile * BM), yc = pass * BN;
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
       for (int64_t w = blockIdx.x; w < a.n_work && !*abort_flag; w += gridDim.x, ++acc_it) {
         {
           const uint32_t b = acc_it & 1, na = acc_it >> 1;
-          if (na > 0 && !mbar_wait(&acce[b], (na - 1) & 1, abort_flag)) { *abort_flag = 1; break; }
+          if (na > 0 && !mbar_wait(&acce[b], (na - 1) & 1, abort_flag, a.wait_limit)) { *abort_flag = 1; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t dtm = tmem + b * BN;
           int zlo, zhi;
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
           for (int kc = 0; kc < a.k_chunks; ++kc) {
             if (chunk_zero(a, kc, zlo, zhi)) continue;   // chunk 0 never is: the first MMA sets D
             const uint32_t s = it % STAGES, n = it / STAGES;
-            if (!mbar_wait(&full[s], n & 1, abort_flag)) { *abort_flag = 1; break; }
+            if (!mbar_wait(&full[s], n & 1, abort_flag, a.wait_limit)) { *abort_flag = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             unsigned char* st = ring + s * STAGE_BYTES;
 #pragma unroll
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_grade_tc(const __grid_constant__
         const uint32_t b = acc_it & 1, na = acc_it >> 1;
         ++acc_it;
         bool ok = true;
-        if (lane == 0) ok = mbar_wait(&accf[b], na & 1, abort_flag);
+        if (lane == 0) ok = mbar_wait(&accf[b], na & 1, abort_flag, a.wait_limit);
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         if (!ok) { if (lane == 0) *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -389,8 +392,6 @@ void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, in
   const float* xl = xh + ld * ld;
   const CUtensorMap mAh = make_map(hi, N, ld, BM), mAl = make_map(lo, N, ld, BM);
   const CUtensorMap mBh = make_map(xh, ld, ld, BN), mBl = make_map(xl, ld, ld, BN);
-  md->err_flag.ensure(sizeof(unsigned), s);
-  MTP_CUDA(cudaMemsetAsync(md->err_flag.p, 0, sizeof(unsigned), s));
   TcArgs a;
   a.N = N;
   a.m = static_cast<int>(md->m_active);
@@ -403,7 +404,9 @@ void run_grade_tc(mtp_model* md, int64_t N, const float* hi, const float* lo, in
   a.parg = reinterpret_cast<int32_t*>(a.pbest + static_cast<size_t>(a.n_pass) * N);
   // partials start as NaN: a pass that does not run (a bounded wait expired) leaves gamma NaN
   MTP_CUDA(cudaMemsetAsync(a.pbest, 0xFF, static_cast<size_t>(a.n_pass) * N * sizeof(float), s));
-  a.err = md->err_flag.as<unsigned>();
+  a.err = md->async_err.as<unsigned>();
+  // host-side fault injection: a single try per wait makes the first unsatisfied wait expire
+  a.wait_limit = take_injected(g_inject_grade_wait) ? 1u : WAIT_LIMIT;
   a.zrow = zrow;
   a.off_c = md->sched.n_types + md->sched.n_lin;
   a.cbn = md->sched.n_types * md->sched.n_rad * md->sched.n_q;

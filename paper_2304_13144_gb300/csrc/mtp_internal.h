@@ -172,6 +172,9 @@ struct mtp_model {
   mtp::DevBuf ws_misc;
   mtp::DevBuf ws_red;          // reductions
   mtp::DevBuf err_flag;        // unsigned
+  // errors of asynchronous kernels (bit 1: a bounded wait of the tensor-core grade expired),
+  // allocated and zeroed by mtp_load, OR-ed by the kernels, read and cleared by mtp_sync
+  mtp::DevBuf async_err;
   bool force_generic = false;  // route the mixed path through the generic kernel (cross-checks)
   // launch shape of the per-neighborhood kernels: warps per block (0 = largest that fits),
   // chosen by mtp_autotune; last_warps records the shape of the latest launch
@@ -181,6 +184,17 @@ struct mtp_model {
   int tune_warps_generic = 0;
   int last_warps = 0;
   bool last_fast = false;
+  // mixed pass: caller's choice (0 automatic, 1 single kernel, 2 three kernels), the
+  // autotuner's choice for "automatic" (-1 untuned, 0 single, 1 three kernels), and the
+  // three-kernel pass's warps per block of its per-pair kernels and neighborhoods per warp of its
+  // contraction (0: defaults)
+  int mixed_pass = 0;
+  int tune_split = -1;
+  int tune_split_warps = 0;
+  int tune_split_nb = 0;
+  bool last_split = false;
+  mtp::DevBuf split_tab;       // slot -> component table of the split pass (uploaded by mtp_load)
+  mtp::DevBuf ws_mom;          // moments / their adjoints of the split pass
 };
 
 struct mtp_nbr {
@@ -219,6 +233,9 @@ struct SiteOutputs {
   const int64_t* atom_list = nullptr;  // optional explicit atoms (rows follow list order)
   const int64_t* row_pos = nullptr;    // optional row of each atom's b_i (rows in another order)
   int64_t n_list = 0;
+  // workspace of the three-kernel mixed pass (moments, then their adjoints; split_ldm(n_mom)
+  // floats per atom); null: the single-kernel pass
+  float* mom = nullptr;
   // tangent mode (training)
   const double* U = nullptr;    // per atom 3
   const double* Scfg = nullptr; // per config 9
@@ -241,15 +258,26 @@ void run_config_gamma_max(const mtp_nbr* nb, const double* gamma, double* gamma_
                           cudaStream_t s);
 void run_classify(const double* gamma, int64_t n, double g_save, double g_break, int32_t* cls, cudaStream_t s);
 void run_widen_argmax(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
+// g_theta = sum_k gE[k] R[k] (R: n_cfg x m configuration rows), g_pos[i] = -gE[cfg(i)] F[i]
+void run_energy_vjp(const mtp_nbr* nb, const double* R, const double* gE, int64_t m, const double* F, double* g_pos,
+                    double* g_theta, cudaStream_t s);
 int64_t run_cut_clusters(const mtp_batch* b, const int64_t* centers, int64_t n, double radius, int64_t* off,
                          double* pos, int32_t* type, int64_t* src, int64_t capacity, cudaStream_t s);
 // host-side fault injection (mtp_debug_inject): armed counts, each consumed by one event
 extern std::atomic<int> g_inject_alloc;
 extern std::atomic<int> g_inject_overflow;
+extern std::atomic<int> g_inject_grade_wait;
 bool take_injected(std::atomic<int>& c);
 // per-neighborhood value slots of the specialised kernel's shared-memory arrays: the values,
 // one always-zero slot (index n_values), padded to a multiple of 4
 inline int padded_nv(int n_values) { return (n_values + 1 + 3) & ~3; }
+// per-atom stride (floats) of the split pass's moment workspace
+inline int split_ldm(int n_mom) { return (n_mom + 3) & ~3; }
+void split_prepare(mtp_model* m);
+// whether the mixed path takes the three-kernel pass (caller's setting, else the autotuner's)
+inline bool split_wanted(const mtp_model* m) {
+  return m->split_tab.p && (m->mixed_pass == 2 || (m->mixed_pass == 0 && m->tune_split != 0));
+}
 int64_t run_maxvol(mtp_model* md, const double* B, int64_t n, double eps, int64_t max_swaps, int64_t* source,
                    cudaStream_t s);
 void run_grade(mtp_model* m, int64_t N, bool fp64, const double* rows, const float* rows_hi,
@@ -263,6 +291,10 @@ void run_train_prep(const mtp_nbr* nb, int n_cfg, const double* E, const double*
                     double w_f, double w_s, double* coef, double* U, double* Scfg, double* loss,
                     DevBuf& tmp, cudaStream_t s);
 void run_sum_rows(const double* part, int nrows, int64_t m, double* out, cudaStream_t s);
+// argument checks shared by the entry points that run the per-neighborhood pass
+void check_run(const mtp_model* m, const mtp_batch* b, const mtp_nbr* nb);
+// loads the allocation-free path's module on `device` (current) and records its scratch address
+void noalloc_prepare(int device);
 int64_t grade_tc_ld(int64_t m);   // row stride of the split parameter rows and of A^-1
 
 }  // namespace mtp

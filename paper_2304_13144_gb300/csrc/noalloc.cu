@@ -6,11 +6,14 @@
 // synchronisation and its possible failure are not acceptable.  This entry point runs the same
 // kernels as mtp_energy_forces_stress but keeps its scratch (per-pair gradients, per-atom
 // energies and virials, per-segment partial sums) in one file-scope device array of fixed size
-// instead of the model's workspace.  The array is part of the library image: every GPU that
-// loads the library holds it until the process exits.  The first call on a device looks up the
-// array's device address (cudaGetSymbolAddress), so that first call should come before any
-// stream capture.  All calls share the one array: calls whose work overlaps on the GPU (other
-// streams, other threads) race on it and must be serialised by the caller.
+// instead of the model's workspace.  The array belongs to this file's device module: the CUDA
+// runtime commits it on a device when the module is loaded there, which mtp_load forces (it
+// looks up the array's device address with the model's device current), so the memory is taken
+// when a model is created, not at the first call, and stays until the process exits.  A call on
+// a device where no model was loaded since the last device reset looks the address up itself,
+// so that first call should come before any stream capture.  All calls share the one array:
+// calls whose work overlaps on the GPU (other streams, other threads) race on it and must be
+// serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,11 +44,13 @@ static __device__ __align__(256) unsigned char g_efs_scratch[kScratchBytes];
 std::mutex g_mu;
 void* g_addr[256] = {nullptr};
 
-// Device address of the scratch array on the current device (looked up once per device).
-void* scratch_address(int device) {
+// Device address of the scratch array on `device` (the current device); refresh = look it up
+// again even if known (mtp_load does, so a model created after a device reset sees the array
+// of the new context; models themselves do not survive a reset).
+void* scratch_address(int device, bool refresh) {
   if (device < 0 || device >= 256) throw Fail{MTP_ERR_ARG, "device index out of range"};
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[device]) {
+  if (refresh || !g_addr[device]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_efs_scratch);
     if (e != cudaSuccess || !p)
@@ -56,6 +61,11 @@ void* scratch_address(int device) {
 }
 
 }  // namespace
+
+// Called by mtp_load with the model's device current: loads this file's module on the device
+// (committing the scratch array there) and records the array's address.
+void noalloc_prepare(int device) { scratch_address(device, true); }
+
 }  // namespace mtp
 
 using namespace mtp;
@@ -64,21 +74,20 @@ extern "C" mtp_status mtp_energy_forces_stress_noalloc(mtp_model* md, const mtp_
                                                        mtp_precision prec, double* energy, double* site_energy,
                                                        double* forces, double* virial, void* stream) {
   try {
-    if (!md || !b || !nb) throw Fail{MTP_ERR_ARG, "null model, batch or neighbor list"};
-    int dev = -1;
-    MTP_CUDA(cudaGetDevice(&dev));
-    if (dev != md->device) throw Fail{MTP_ERR_ARG, "model belongs to another device"};
-    if (b->n_cfg != nb->n_cfg) throw Fail{MTP_ERR_ARG, "neighbor list was built for another batch"};
+    check_run(md, b, nb);
     if (prec != MTP_FP64 && prec != MTP_MIXED) throw Fail{MTP_ERR_ARG, "unknown precision"};
     if (!energy && !site_energy && !forces && !virial) throw Fail{MTP_ERR_ARG, "no output requested"};
     if (nb->n_atoms > kMaxAtoms || nb->n_pairs > kMaxPairs || nb->n_seg > kMaxSegments)
       throw Fail{MTP_ERR_CAPACITY, "the allocation-free path holds at most " + std::to_string(kMaxAtoms) + " atoms, " +
                                        std::to_string(kMaxPairs) + " pairs and " + std::to_string(kMaxSegments) +
                                        " configuration segments; this call has " + std::to_string(nb->n_atoms) +
-                                       " atoms and " + std::to_string(nb->n_pairs) + " pairs"};
+                                       " atoms, " + std::to_string(nb->n_pairs) + " pairs and " +
+                                       std::to_string(nb->n_seg) + " segments"};
     const bool fp64 = prec == MTP_FP64;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned char* base = static_cast<unsigned char*>(scratch_address(dev));
+    int dev = -1;
+    MTP_CUDA(cudaGetDevice(&dev));
+    unsigned char* base = static_cast<unsigned char*>(scratch_address(dev, false));
     unsigned char* pG = base;
     double* pV = reinterpret_cast<double*>(base + align_up(kMaxPairs * 3 * sizeof(double)));
     double* pW = pV + align_up(kMaxAtoms * sizeof(double)) / sizeof(double);

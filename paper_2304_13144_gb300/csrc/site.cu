@@ -493,9 +493,12 @@ int site_max_grid(mtp_model* m, bool fp64, bool tangent) {
 }
 
 bool run_sites_fast(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const SiteOutputs& o, cudaStream_t s);
+bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const SiteOutputs& o, cudaStream_t s);
 
 void run_sites(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, bool fp64, const SiteOutputs& o,
                bool tangent, int* grid_used, cudaStream_t s) {
+  m->last_split = false;
+  if (!fp64 && !tangent && !m->force_generic && run_sites_split(m, b, nb, o, s)) return;
   if (!fp64 && !tangent && !m->force_generic && run_sites_fast(m, b, nb, o, s)) return;
   SiteParams P{};
   P.warps_hint = m->tune_warps_generic;

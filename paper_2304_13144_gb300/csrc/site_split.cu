@@ -1,0 +1,802 @@
+// Mixed-path (FP32 arithmetic, FP64 sums) per-neighborhood pass as three kernels, each laid
+// out for its own phase of the method:
+//
+//   k_moments   (eqs. 3-4)  8 lanes per neighborhood, 4 neighborhoods per warp.  The lanes
+//               stage their pairs' r_ij and f_mu(r_ij) in shared memory, then for every
+//               32-component chunk of the moment set each lane sums f_mu x^a y^b z^c over its
+//               own pairs in registers and one 3-stage butterfly over the 8 lanes leaves each
+//               lane with 4 component sums.  Output: the moments, FP32, [work x ldm].
+//   k_contract  (eqs. 2, 5-6 and their adjoint)  one or two neighborhoods per warp carried
+//               through the contraction schedule (32-lane slabs of packed triples in shared
+//               memory, as in site_fast.cu), V_i = s_z + sum_a xi_a B_a, the reverse pass seeded
+//               with xi, and the adjoints dV/dM written over the moments.  The basis part of
+//               the parameter row b_i (eq. 9) is written here.
+//   k_adjoint   (forces and virial; the radial block of eq. 9)  8 lanes per neighborhood: per
+//               pair dV_i/dr_ij from dV/dM (monomials regenerated in registers), the per-pair
+//               gradients for the force gather, the neighborhood's virial, and
+//               sum_j g_mu(j) Q_b(r_ij) per neighbor species for b_i.
+//
+// Splitting frees each phase from the others' resources: the contraction runs without the
+// per-pair phases' 255 registers (more warps per SM, deeper unrolling), and the per-pair phases
+// fill their lanes (about 44 pairs over 8 lanes use 92 % of the lane slots; 32 lanes per
+// neighborhood used 69 %).  The moments and their adjoints cross HBM once each way
+// (4 ldm bytes per atom, each way).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "mtp_internal.h"
+#include "profiler.h"
+#include "site_shape.h"
+
+namespace mtp {
+namespace {
+using namespace shape;
+
+constexpr int kNQs = 8;      // radial polynomials of the specialised kernels
+constexpr int LPN = 8;       // lanes per neighborhood in the per-pair kernels
+constexpr int GPW = 32 / LPN;
+constexpr int BATCH = 64;    // pairs staged per neighborhood at a time
+
+struct SplitArgs {
+  DevSchedule d;
+  DevNbr nb;
+  const int* type;
+  int64_t n_work;
+  SiteOutputs o;
+  float* mom;   // [n_work x ldm]: moments (k_moments), overwritten by dV/dM (k_contract), both in
+                // slot order (monomial-major, the order of the moment pass's chunks)
+  int ldm;
+  const int* slot_comp;   // slot -> value index of the moment component
+  int T, CBN, NC, NV;
+  // contraction kernel: shared-memory layout (word offsets of the schedule arrays)
+  size_t c_bytes, sched_bytes, warp_bytes, total;
+  int o_fslab, o_fround, o_frdst, o_rslab, o_rround, o_rrval, o_seed;
+};
+
+__device__ __forceinline__ int64_t atom_of(const SplitArgs& P, int64_t wk) {
+  return P.o.atom_list ? P.o.atom_list[wk] : wk;
+}
+
+// Range-checked element access (compiled in with MTP_SPLIT_CHECK): an index outside [0, n) is
+// recorded (the first one: check code and index) and the access goes to a scratch slot instead.
+#ifdef MTP_SPLIT_CHECK
+__device__ unsigned long long g_split_fault;
+__device__ __align__(16) unsigned char g_split_dummy[64];
+template <class T>
+__device__ __forceinline__ T& AT(T* p, long long i, long long n, int code) {
+  if (i < 0 || i >= n) {
+    atomicCAS(&g_split_fault, 0ull,
+              (static_cast<unsigned long long>(code) << 48) | (static_cast<unsigned long long>(i) & 0xFFFFFFFFFFFFull));
+    return *reinterpret_cast<T*>(g_split_dummy);
+  }
+  return p[i];
+}
+__device__ __forceinline__ bool OK(long long i, long long n, int code) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_split_fault, 0ull,
+            (static_cast<unsigned long long>(code) << 48) | (static_cast<unsigned long long>(i) & 0xFFFFFFFFFFFFull));
+  return false;
+}
+#else
+template <class T>
+__device__ __forceinline__ T& AT(T* p, long long i, long long, int) { return p[i]; }
+__device__ __forceinline__ constexpr bool OK(long long, long long, int) { return true; }
+#endif
+
+// v[0..31] on each of the LPN lanes of a group -> lane q of the group holds, in v[0..3], the sums
+// over the group of components 4q .. 4q+3 (recursive halving: the lane with bit s of q set keeps
+// the upper half and receives its partner's upper half)
+__device__ __forceinline__ void group_reduce32(float (&v)[32], int q) {
+  static_assert(LPN == 8, "the butterfly is written for 8 lanes");
+  static_for<0, 3>([&](auto S) {
+    constexpr int st = decltype(S)::value;
+    constexpr int s = 4 >> st;        // partner distance 4, 2, 1
+    constexpr int h = 16 >> st;       // values exchanged: 16, 8, 4
+    const bool up = (q & s) != 0;
+    static_for<0, h>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const float send = up ? v[i] : v[i + h];
+      const float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    });
+  });
+}
+
+__device__ __forceinline__ float group_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// x^A y^B z^C from the power tables (compile-time exponents, no multiply by 1)
+template <int A, int B, int C, int D>
+__device__ __forceinline__ float mono_of(const float (&px)[D], const float (&py)[D], const float (&pz)[D]) {
+  if constexpr (A + B + C == 0) {
+    return 1.f;
+  } else if constexpr (A > 0 && B > 0 && C > 0) {
+    return px[A] * py[B] * pz[C];
+  } else if constexpr (A > 0 && B > 0) {
+    return px[A] * py[B];
+  } else if constexpr (A > 0 && C > 0) {
+    return px[A] * pz[C];
+  } else if constexpr (B > 0 && C > 0) {
+    return py[B] * pz[C];
+  } else if constexpr (A > 0) {
+    return px[A];
+  } else if constexpr (B > 0) {
+    return py[B];
+  } else {
+    return pz[C];
+  }
+}
+
+template <int NR, int NU0>
+struct ChunkInfo {
+  using Sh = Shape<NR, NU0>;
+  using Tb = Tab<NR, NU0>;
+  static constexpr int deg_hi(int c) {
+    int d = 0;
+    for (int s = 32 * c; s < 32 * c + 32 && s < Sh::NCOMP; ++s) d = Tb::mono.deg[Tb::slots.k[s]] > d ? Tb::mono.deg[Tb::slots.k[s]] : d;
+    return d;
+  }
+};
+
+// ------------------------------------------------------------------------------------
+// moments (eqs. 3-4)
+// ------------------------------------------------------------------------------------
+template <int NR, int NU0>
+__global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
+  using Sh = Shape<NR, NU0>;
+  using Tb = Tab<NR, NU0>;
+  using CI = ChunkInfo<NR, NU0>;
+  constexpr int NQ = kNQs;
+  constexpr int PS = (3 + NR + 3) & ~3;   // staged floats per pair: x, y, z, f_0 .. f_{NR-1}
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DevSchedule& d = P.d;
+  float* ctab = reinterpret_cast<float*>(smem);
+  const int T = P.T;
+  for (int k = threadIdx.x; k < P.NC; k += blockDim.x)
+    if (OK(T + d.n_lin + k, d.n_params, 1)) ctab[k] = d.theta_f[T + d.n_lin + k];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / LPN, q = lane % LPN;
+  const int nwarps = blockDim.x >> 5;
+  float* stg = reinterpret_cast<float*>(smem + P.c_bytes) + (static_cast<size_t>(warp) * GPW + grp) * BATCH * PS;
+  __syncthreads();
+  const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
+  for (int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * GPW; w0 < P.n_work;
+       w0 += static_cast<int64_t>(gridDim.x) * nwarps * GPW) {
+    const int64_t wk = w0 + grp;
+    const bool live = wk < P.n_work;
+    int np = 0, zi = 0;
+    int64_t p0 = 0;
+    if (live && OK(wk, P.nb.n_atoms, 3)) {
+      const int64_t i = atom_of(P, wk);
+      zi = P.type[i];
+      p0 = P.nb.off[i];
+      np = static_cast<int>(P.nb.off[i + 1] - p0);
+      if (!OK(zi, T, 4) || !OK(p0 + np - 1 + (np == 0), P.nb.n_pairs + 1, 5)) { zi = 0; np = 0; }
+    }
+    // the warp walks the batches of its largest neighborhood (all lanes take part in the butterflies)
+    int np_max = np;
+    for (int m = 16; m; m >>= 1) np_max = max(np_max, __shfl_xor_sync(0xffffffffu, np_max, m));
+    const float* czi = ctab + static_cast<size_t>(zi) * T * NR * NQ;
+    float* out = live ? P.mom + wk * P.ldm : nullptr;
+    // at least one pass, so that a neighborhood without pairs gets zero moments
+    for (int base = 0; base < max(np_max, 1); base += BATCH) {
+      const int nbt = min(BATCH, np - base);   // <= 0 for a group that is done
+      __syncwarp();
+      for (int t = q; t < nbt; t += LPN) {
+        const int64_t p = p0 + base + t;
+        if (!OK(p, P.nb.n_pairs, 6) || !OK(t * PS + PS - 1, BATCH * PS, 7)) continue;
+        const float4 r = P.nb.pr32[p];
+        const int jj = P.nb.pj[p];
+        if (!OK(jj, P.nb.n_atoms, 8)) continue;
+        const int zj = P.type[jj];
+        if (!OK(zj, T, 9)) continue;
+        float f[NR], df[NR];
+        radial<NR, NQ>(r.w, czi + zj * NR * NQ, rmin, rcut, f, df, nullptr);
+        float* e = stg + t * PS;
+        e[0] = r.x; e[1] = r.y; e[2] = r.z;
+#pragma unroll
+        for (int mu = 0; mu < NR; ++mu) e[3 + mu] = f[mu];
+      }
+      __syncwarp();
+      static_for<0, Sh::NCHUNK>([&](auto Cc) {
+        constexpr int c = decltype(Cc)::value;
+        constexpr int DH = CI::deg_hi(c);
+        float acc[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) acc[t] = 0.f;
+        for (int t = q; t < nbt; t += LPN) {
+          if (!OK(t * PS + PS - 1, BATCH * PS, 10)) continue;
+          const float* e = stg + t * PS;
+          const float x = e[0], y = e[1], z = e[2];
+          float f[NR];
+#pragma unroll
+          for (int mu = 0; mu < NR; ++mu) f[mu] = e[3 + mu];
+          float px[DH + 1], py[DH + 1], pz[DH + 1];
+          px[0] = py[0] = pz[0] = 1.f;
+#pragma unroll
+          for (int k = 1; k <= DH; ++k) {
+            px[k] = k == 1 ? x : px[k - 1] * x;
+            py[k] = k == 1 ? y : py[k - 1] * y;
+            pz[k] = k == 1 ? z : pz[k - 1] * z;
+          }
+          float mk = 0.f;
+          static_for<0, 32>([&](auto Tt) {
+            constexpr int t2 = decltype(Tt)::value;
+            constexpr int s = 32 * c + t2;
+            if constexpr (s < Sh::NCOMP) {
+              constexpr int k = Tb::slots.k[s];
+              constexpr int mu = Tb::slots.mu[s];
+              constexpr bool fresh = (t2 == 0) ? true : (Tb::slots.k[s > 0 ? s - 1 : 0] != k);
+              if constexpr (fresh) mk = mono_of<Tb::mono.a[k], Tb::mono.b[k], Tb::mono.c[k]>(px, py, pz);
+              acc[t2] = fmaf(f[mu], mk, acc[t2]);
+            }
+          });
+        }
+        group_reduce32(acc, q);
+        // lane q holds slots 32c + 4q .. +3 (zeros past the last slot; ldm covers them)
+        if (live && 32 * c + 4 * q < Sh::NCOMP && OK(wk * P.ldm + 32 * c + 4 * q + 3, P.n_work * P.ldm, 11)) {
+          float4* o4 = reinterpret_cast<float4*>(out + 32 * c + 4 * q);
+          float4 val = make_float4(acc[0], acc[1], acc[2], acc[3]);
+          if (base > 0) {
+            const float4 prev = *o4;
+            val.x += prev.x; val.y += prev.y; val.z += prev.z; val.w += prev.w;
+          }
+          *o4 = val;
+        }
+      });
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// contraction and its adjoint (eqs. 2, 5-6); NB neighborhoods per warp
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void copy_words_s(uint32_t* dst, const uint32_t* src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+template <int NB, bool INL>
+__global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DevSchedule& d = P.d;
+  const int NV = P.NV;
+  float* coef = reinterpret_cast<float*>(smem);
+  for (int k = threadIdx.x; k < d.n_coef; k += blockDim.x)
+    if (OK(k * 4 + 3, static_cast<long long>(P.c_bytes), 20)) coef[k] = d.coef_f[k];
+  uint32_t* sched = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
+  copy_words_s(sched + P.o_fslab, d.fslab, d.fslab_words);
+  copy_words_s(sched + P.o_fround, reinterpret_cast<const uint32_t*>(d.fround), 4 * d.n_fround);
+  copy_words_s(sched + P.o_frdst, reinterpret_cast<const uint32_t*>(d.fr_dst), 32 * d.n_fround);
+  copy_words_s(sched + P.o_rslab, d.rslab, d.rslab_words);
+  copy_words_s(sched + P.o_rround, reinterpret_cast<const uint32_t*>(d.rround), 4 * d.n_rround);
+  copy_words_s(sched + P.o_rrval, reinterpret_cast<const uint32_t*>(d.rr_val), 32 * d.n_rround);
+  copy_words_s(sched + P.o_seed, reinterpret_cast<const uint32_t*>(d.seed_f), d.n_vals);
+  const uint32_t* s_fslab = sched + P.o_fslab;
+  const int4* s_fround = reinterpret_cast<const int4*>(sched + P.o_fround);
+  const int* s_frdst = reinterpret_cast<const int*>(sched + P.o_frdst);
+  const uint32_t* s_rslab = sched + P.o_rslab;
+  const int4* s_rround = reinterpret_cast<const int4*>(sched + P.o_rround);
+  const int* s_rrval = reinterpret_cast<const int*>(sched + P.o_rrval);
+  const float* s_seed = reinterpret_cast<const float*>(sched + P.o_seed);
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per warp: NB (values, adjoints) array pairs, each adjoint array NV after its values
+  float* const wbase = reinterpret_cast<float*>(smem + P.c_bytes + P.sched_bytes + warp * P.warp_bytes);
+  for (int k = lane; k < 2 * NB * NV; k += 32) wbase[k] = 0.f;   // the zero slot n_vals stays 0
+  __syncthreads();
+  const int T = P.T;
+  const int n_mom = d.n_mom;
+  auto decode = [&](uint32_t w, float& c, uint32_t& x, uint32_t& y) {
+    if constexpr (INL) {
+      c = __uint_as_float(((w >> 22) << 17) + 0x3F800000u);
+      x = w & 2047u;
+      y = (w >> 11) & 2047u;
+    } else {
+      c = coef[w >> 24];
+      x = w & 4095u;
+      y = (w >> 12) & 4095u;
+    }
+  };
+  for (int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * NB; w0 < P.n_work;
+       w0 += static_cast<int64_t>(gridDim.x) * nwarps * NB) {
+    float* v[NB];
+    float* g[NB];
+    int64_t wk[NB];
+    bool live[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      v[j] = wbase + 2 * j * NV;
+      g[j] = v[j] + NV;
+      wk[j] = w0 + j;
+      live[j] = wk[j] < P.n_work;
+      const float* src = P.mom + (live[j] ? wk[j] : w0) * P.ldm;
+      for (int k = lane; k < n_mom; k += 32) {
+        const int sc = P.slot_comp[k];
+        if (OK(sc, NV, 21) && OK((live[j] ? wk[j] : w0) * P.ldm + k, P.n_work * P.ldm, 22))
+          v[j][sc] = live[j] ? __ldcs(src + k) : 0.f;
+      }
+    }
+    __syncwarp();
+    // ---------------- forward contraction ----------------
+    int4 rd_n = d.n_fround > 0 ? s_fround[0] : make_int4(0, 0, 0, 0);
+    int dst_n = d.n_fround > 0 ? s_frdst[lane] : -1;
+    for (int r = 0; r < d.n_fround; ++r) {
+      int4 rd = rd_n;
+      const int dst = dst_n;
+      if (r + 1 < d.n_fround) {
+        rd_n = s_fround[r + 1];
+        dst_n = s_frdst[32 * (r + 1) + lane];
+      }
+      const uint32_t* slab = s_fslab + rd.y + lane;
+      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.fslab_words, 23)) { rd.x = 0; }
+      float a0[NB], a1[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) { a0[j] = 0.f; a1[j] = 0.f; }
+      int it = 0;
+      for (; it + 4 <= rd.x; it += 4) {
+        const uint32_t w0_ = slab[32 * it], w1_ = slab[32 * it + 32], w2_ = slab[32 * it + 64], w3_ = slab[32 * it + 96];
+        float c0, c1, c2, c3;
+        uint32_t x0, y0, x1, y1, x2, y2, x3, y3;
+        decode(w0_, c0, x0, y0);
+        decode(w1_, c1, x1, y1);
+        decode(w2_, c2, x2, y2);
+        decode(w3_, c3, x3, y3);
+        if (!OK(x0, NV, 24) || !OK(y0, NV, 24) || !OK(x1, NV, 24) || !OK(y1, NV, 24) || !OK(x2, NV, 24) ||
+            !OK(y2, NV, 24) || !OK(x3, NV, 24) || !OK(y3, NV, 24)) continue;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          a0[j] = fmaf(c0, v[j][x0] * v[j][y0], a0[j]);
+          a1[j] = fmaf(c1, v[j][x1] * v[j][y1], a1[j]);
+          a0[j] = fmaf(c2, v[j][x2] * v[j][y2], a0[j]);
+          a1[j] = fmaf(c3, v[j][x3] * v[j][y3], a1[j]);
+        }
+      }
+      for (; it < rd.x; ++it) {
+        float c0;
+        uint32_t x0, y0;
+        decode(slab[32 * it], c0, x0, y0);
+        if (!OK(x0, NV, 25) || !OK(y0, NV, 25)) continue;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) a0[j] = fmaf(c0, v[j][x0] * v[j][y0], a0[j]);
+      }
+      if (dst >= 0 && OK(dst, NV, 26)) {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) v[j][dst] = a0[j] + a1[j];
+      }
+      if (rd.z) __syncwarp();
+    }
+    // ---------------- site energy (eq. 2) ----------------
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (!live[j]) continue;
+      const int64_t i = atom_of(P, wk[j]);
+      if (P.o.V) {
+        float acc = 0.f;
+        for (int a = lane; a < d.n_lin; a += 32)
+          if (OK(d.basis_idx[a], NV, 27)) acc = fmaf(d.theta_f[T + a], v[j][d.basis_idx[a]], acc);
+        for (int m = 16; m; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+        if (lane == 0) P.o.V[i] = static_cast<double>(acc) + d.theta_d[P.type[i]];
+      }
+    }
+    // ---------------- adjoint of the contraction (gather form) ----------------
+    rd_n = d.n_rround > 0 ? s_rround[0] : make_int4(0, 0, 0, 0);
+    int x_n = d.n_rround > 0 ? s_rrval[lane] : -1;
+    for (int r = 0; r < d.n_rround; ++r) {
+      int4 rd = rd_n;
+      const int x = x_n;
+      if (r + 1 < d.n_rround) {
+        rd_n = s_rround[r + 1];
+        x_n = s_rrval[32 * (r + 1) + lane];
+      }
+      const float sd = (x >= 0 && OK(x, d.n_vals, 28)) ? s_seed[x] : 0.f;
+      const uint32_t* slab = s_rslab + rd.y + lane;
+      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.rslab_words, 29)) { rd.x = 0; }
+      float a0[NB], a1[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) { a0[j] = sd; a1[j] = 0.f; }
+      int it = 0;
+      for (; it + 4 <= rd.x; it += 4) {
+        const uint32_t w0_ = slab[32 * it], w1_ = slab[32 * it + 32], w2_ = slab[32 * it + 64], w3_ = slab[32 * it + 96];
+        float c0, c1, c2, c3;
+        uint32_t x0, y0, x1, y1, x2, y2, x3, y3;
+        decode(w0_, c0, x0, y0);
+        decode(w1_, c1, x1, y1);
+        decode(w2_, c2, x2, y2);
+        decode(w3_, c3, x3, y3);
+        if (!OK(x0, NV, 30) || !OK(y0, NV, 30) || !OK(x1, NV, 30) || !OK(y1, NV, 30) || !OK(x2, NV, 30) ||
+            !OK(y2, NV, 30) || !OK(x3, NV, 30) || !OK(y3, NV, 30)) continue;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          a0[j] = fmaf(c0, v[j][x0] * g[j][y0], a0[j]);
+          a1[j] = fmaf(c1, v[j][x1] * g[j][y1], a1[j]);
+          a0[j] = fmaf(c2, v[j][x2] * g[j][y2], a0[j]);
+          a1[j] = fmaf(c3, v[j][x3] * g[j][y3], a1[j]);
+        }
+      }
+      for (; it < rd.x; ++it) {
+        float c0;
+        uint32_t x0, y0;
+        decode(slab[32 * it], c0, x0, y0);
+        if (!OK(x0, NV, 31) || !OK(y0, NV, 31)) continue;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) a0[j] = fmaf(c0, v[j][x0] * g[j][y0], a0[j]);
+      }
+      if (x >= 0 && OK(x, NV, 32)) {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) g[j][x] = a0[j] + a1[j];
+      }
+      if (rd.z) __syncwarp();
+    }
+    __syncwarp();
+    // ---------------- outputs: dV/dM over the moments, the basis part of b_i ----------------
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (!live[j]) continue;
+      float* dst = P.mom + wk[j] * P.ldm;
+      for (int k = lane; k < n_mom; k += 32)
+        if (OK(P.slot_comp[k], NV, 33) && OK(wk[j] * P.ldm + k, P.n_work * P.ldm, 34)) __stcs(dst + k, g[j][P.slot_comp[k]]);
+      const int64_t i = atom_of(P, wk[j]);
+      const int64_t rw = P.o.row_pos ? P.o.row_pos[i] : wk[j];
+      if (P.o.rows_hi) {
+        const int zi = P.type[i];
+        float* hi = P.o.rows_hi + rw * P.o.rows_ld;
+        float* lo = P.o.rows_lo ? P.o.rows_lo + rw * P.o.rows_ld : nullptr;
+        for (int k = lane; k < T + d.n_lin; k += 32) {
+          if (!OK(rw * P.o.rows_ld + k, P.nb.n_atoms * P.o.rows_ld, 35)) continue;
+          if (k >= T && !OK(d.basis_idx[k - T], NV, 36)) continue;
+          const float val = k < T ? (k == zi ? 1.f : 0.f) : v[j][d.basis_idx[k - T]];
+          if (lo) {
+            const float h = tf32_rn(val);
+            __stcs(hi + k, h);
+            __stcs(lo + k, tf32_rn(val - h));
+          } else {
+            __stcs(hi + k, val);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// pair adjoint: per-pair gradients, the neighborhood's virial, the radial block of b_i
+// ------------------------------------------------------------------------------------
+template <int NR, int NU0, bool ROWS>
+__global__ void __launch_bounds__(256) k_adjoint(SplitArgs P) {
+  using Sh = Shape<NR, NU0>;
+  constexpr int NQ = kNQs;
+  constexpr int GS = (NR + NQ + 1 + 3) & ~3;   // staged per pair for the radial block: g_mu, Q_b, species
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DevSchedule& d = P.d;
+  const int T = P.T;
+  float* ctab = reinterpret_cast<float*>(smem);
+  for (int k = threadIdx.x; k < P.NC; k += blockDim.x) ctab[k] = d.theta_f[T + d.n_lin + k];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / LPN, q = lane % LPN;
+  const int nwarps = blockDim.x >> 5;
+  // per group: dV/dM (ldm + 8 floats: the 8-float skew puts the 4 groups' arrays in distinct
+  // banks, so a broadcast read of one component by all groups is one wavefront), then the
+  // radial-block staging (BATCH x GS)
+  const int gstride = P.ldm + 8 + (ROWS ? BATCH * GS : 0);
+  float* gM = reinterpret_cast<float*>(smem + P.c_bytes) + (static_cast<size_t>(warp) * GPW + grp) * gstride;
+  float* rstg = gM + P.ldm + 8;
+  __syncthreads();
+  const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
+  for (int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * GPW; w0 < P.n_work;
+       w0 += static_cast<int64_t>(gridDim.x) * nwarps * GPW) {
+    const int64_t wk = w0 + grp;
+    const bool live = wk < P.n_work;
+    int np = 0, zi = 0;
+    int64_t p0 = 0, i = 0;
+    if (live && OK(wk, P.nb.n_atoms, 40)) {
+      i = atom_of(P, wk);
+      zi = P.type[i];
+      p0 = P.nb.off[i];
+      np = static_cast<int>(P.nb.off[i + 1] - p0);
+      if (!OK(zi, T, 41) || !OK(p0 + np - 1 + (np == 0), P.nb.n_pairs + 1, 42)) { zi = 0; np = 0; }
+    }
+    int np_max = np;
+    for (int m = 16; m; m >>= 1) np_max = max(np_max, __shfl_xor_sync(0xffffffffu, np_max, m));
+    __syncwarp();
+    if (live) {
+      const float* src = P.mom + wk * P.ldm;
+      for (int k = q; k < Sh::NCOMP; k += LPN)
+        if (OK(P.slot_comp[k], P.ldm, 43) && OK(wk * P.ldm + k, P.n_work * P.ldm, 44)) gM[P.slot_comp[k]] = __ldcs(src + k);
+    }
+    __syncwarp();
+    const float* czi = ctab + static_cast<size_t>(zi) * T * NR * NQ;
+    float Wl[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Wl[k] = 0.f;
+    // radial block accumulators: lane q owns beta = q for every (species, mu)
+    float cb[3][NR];
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+      for (int mu = 0; mu < NR; ++mu) cb[z][mu] = 0.f;
+    float* Gout = static_cast<float*>(P.o.G);
+    for (int base = 0; base < np_max; base += BATCH) {
+      const int nbt = min(BATCH, np - base);
+      // every lane of the warp runs the same number of iterations (adjoint_pass has warp-wide
+      // __syncwarp fences); lanes without a pair of their own work on a dummy one
+      const int nbt_w = min(BATCH, np_max - base);
+      for (int t0 = 0; t0 < nbt_w; t0 += LPN) {
+        const int t = t0 + q;
+        const int64_t p = p0 + base + t;
+        bool act = t < nbt;
+        if (act && (!OK(p, P.nb.n_pairs, 45) || (ROWS && !OK(t * GS + GS - 1, BATCH * GS, 46)))) act = false;
+        float4 r = make_float4(1.f, 0.f, 0.f, 1.f);
+        int zj = 0;
+        if (act) {
+          r = P.nb.pr32[p];
+          const int jj = P.nb.pj[p];
+          if (OK(jj, P.nb.n_atoms, 47)) zj = P.type[jj];
+          if (!OK(zj, T, 48)) zj = 0;
+        }
+        float f[NR], df[NR], g[NR];
+        radial<NR, NQ>(r.w, czi + zj * NR * NQ, rmin, rcut, f, df, (ROWS && act) ? rstg + t * GS + NR : nullptr);
+#pragma unroll
+        for (int mu = 0; mu < NR; ++mu) g[mu] = 0.f;
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        adjoint_pass<NR, NU0>(r.x, r.y, r.z, f, gM, g, gx, gy, gz);
+        if (!act) continue;
+        float rad = 0.f;
+#pragma unroll
+        for (int mu = 0; mu < NR; ++mu) rad = fmaf(g[mu], df[mu], rad);
+        const float sc = rad / r.w;
+        gx = fmaf(sc, r.x, gx);
+        gy = fmaf(sc, r.y, gy);
+        gz = fmaf(sc, r.z, gz);
+        if (Gout && OK(3 * p + 2, 3 * P.nb.n_pairs, 53)) {
+          __stcs(Gout + 3 * p + 0, gx);
+          __stcs(Gout + 3 * p + 1, gy);
+          __stcs(Gout + 3 * p + 2, gz);
+        }
+        const float g3[3] = {gx, gy, gz}, r3[3] = {r.x, r.y, r.z};
+#pragma unroll
+        for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+          for (int b2 = 0; b2 < 3; ++b2) Wl[3 * a2 + b2] = fmaf(-g3[a2], r3[b2], Wl[3 * a2 + b2]);
+        if (ROWS) {
+          float* e = rstg + t * GS;
+#pragma unroll
+          for (int mu = 0; mu < NR; ++mu) e[mu] = g[mu];
+          e[NR + NQ] = __int_as_float(zj);
+        }
+      }
+      if (ROWS) {
+        __syncwarp();
+        // sum_j g_mu(j) Q_b(r_ij) per neighbor species: lane q takes b = q over the staged pairs
+        for (int t = 0; t < nbt; ++t) {
+          if (!OK(t * GS + GS - 1, BATCH * GS, 49)) continue;
+          const float* e = rstg + t * GS;
+          const float qb = e[NR + q];
+          const int zj = __float_as_int(e[NR + NQ]);
+#pragma unroll
+          for (int mu = 0; mu < NR; ++mu) {
+            const float pr = e[mu] * qb;
+#pragma unroll
+            for (int z = 0; z < 3; ++z) cb[z][mu] += (zj == z) ? pr : 0.f;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // the neighborhood's virial (FP32 over its pairs, like its forces; sums over atoms are FP64)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Wl[k] = group_sum(Wl[k]);
+    if (live && P.o.Wat && q == 0 && OK(9 * i + 8, 9 * P.nb.n_atoms, 50)) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) P.o.Wat[9 * i + k] = static_cast<double>(Wl[k]);
+    }
+    if (ROWS && live && P.o.rows_hi) {
+      const int64_t rw = P.o.row_pos ? P.o.row_pos[i] : wk;
+      const int64_t ld = P.o.rows_ld;
+      const int off_c = T + d.n_lin;
+      float* hi = P.o.rows_hi + rw * ld;
+      float* lo = P.o.rows_lo ? P.o.rows_lo + rw * ld : nullptr;
+      auto put = [&](int64_t k, float val) {
+        if (!OK(rw * ld + k, P.nb.n_atoms * ld, 51) || !OK(k, ld, 52)) return;
+        if (lo) {
+          const float h = tf32_rn(val);
+          __stcs(hi + k, h);
+          __stcs(lo + k, tf32_rn(val - h));
+        } else {
+          __stcs(hi + k, val);
+        }
+      };
+      // block zi holds the sums; the other species' blocks and the padding past m are zero
+      for (int k = off_c + q; k < ld; k += LPN) {
+        const int e = k - off_c;
+        if (e / P.CBN != zi || k >= d.n_params) put(k, 0.f);
+      }
+#pragma unroll
+      for (int z = 0; z < 3; ++z) {
+        if (z < T) {
+#pragma unroll
+          for (int mu = 0; mu < NR; ++mu) put(off_c + static_cast<int64_t>(zi) * P.CBN + (z * NR + mu) * NQ + q, cb[z][mu]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <class K>
+int blocks_per_sm(K kern, int threads, size_t smem) {
+  int per = 0;
+  MTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem));
+  return std::max(per, 1);
+}
+
+int num_sms() {
+  int dev = 0, nsm = 0;
+  MTP_CUDA(cudaGetDevice(&dev));
+  MTP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  return nsm;
+}
+
+template <int NR, int NU0>
+void launch_split(SplitArgs P, int warps_pair, int nb_contract, bool efs, bool rows, cudaStream_t s) {
+  constexpr int NQ = kNQs;
+  const int nsm = num_sms();
+  const int64_t groups = (P.n_work + GPW - 1) / GPW;
+  // ---- moments ----
+  {
+    constexpr int PS = (3 + NR + 3) & ~3;
+    const size_t smem = P.c_bytes + static_cast<size_t>(warps_pair) * GPW * BATCH * PS * sizeof(float);
+    auto kern = k_moments<NR, NU0>;
+    MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    const int per = blocks_per_sm(kern, warps_pair * 32, smem);
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((groups + warps_pair - 1) / warps_pair,
+                                                                              static_cast<int64_t>(nsm) * per)));
+    ProfRegion pr("site_moments", s);
+    kern<<<grid, warps_pair * 32, smem, s>>>(P);
+    ProfRegion::launched();
+    MTP_CUDA(cudaGetLastError());
+  }
+  // ---- contraction ----
+  {
+    const size_t smem = P.total;
+    const int wpb = std::max(1, static_cast<int>((227 * 1024 - P.c_bytes - P.sched_bytes) / P.warp_bytes));
+    const int warps = std::min(wpb, 16);
+    const bool inl = P.d.coef_inline;
+    auto launch = [&](auto kern) {
+      const size_t sm = P.c_bytes + P.sched_bytes + static_cast<size_t>(warps) * P.warp_bytes;
+      MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+      const int per = blocks_per_sm(kern, warps * 32, sm);
+      const int64_t need = (P.n_work + nb_contract - 1) / nb_contract;
+      const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((need + warps - 1) / warps,
+                                                                                static_cast<int64_t>(nsm) * per)));
+      ProfRegion pr("site_contract", s);
+      kern<<<grid, warps * 32, sm, s>>>(P);
+      ProfRegion::launched();
+      MTP_CUDA(cudaGetLastError());
+    };
+    (void)smem;
+    if (nb_contract == 2) {
+      if (inl) launch(k_contract<2, true>);
+      else launch(k_contract<2, false>);
+    } else {
+      if (inl) launch(k_contract<1, true>);
+      else launch(k_contract<1, false>);
+    }
+  }
+  // ---- pair adjoint ----
+  if (efs || rows) {
+    constexpr int GS = (NR + NQ + 1 + 3) & ~3;
+    const size_t gstride = static_cast<size_t>(P.ldm + 8 + (rows ? BATCH * GS : 0));
+    const size_t smem = P.c_bytes + static_cast<size_t>(warps_pair) * GPW * gstride * sizeof(float);
+    auto go = [&](auto kern) {
+      MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+      const int per = blocks_per_sm(kern, warps_pair * 32, smem);
+      const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((groups + warps_pair - 1) / warps_pair,
+                                                                                static_cast<int64_t>(nsm) * per)));
+      ProfRegion pr("site_adjoint", s);
+      kern<<<grid, warps_pair * 32, smem, s>>>(P);
+      ProfRegion::launched();
+      MTP_CUDA(cudaGetLastError());
+    };
+    if (rows) go(k_adjoint<NR, NU0, true>);
+    else go(k_adjoint<NR, NU0, false>);
+  }
+}
+
+template <int NR, int NU0>
+std::vector<int> slot_table() {
+  using Sh = Shape<NR, NU0>;
+  constexpr auto S = make_slots<NR, NU0>();
+  return std::vector<int>(S.comp, S.comp + Sh::NCOMP);
+}
+
+}  // namespace
+
+// Uploads the slot -> component table of the model's shape (at load time, so that the split
+// pass allocates nothing when it runs); leaves it empty for shapes without a split kernel.
+void split_prepare(mtp_model* m) {
+  const DevSchedule& d = m->ds;
+  std::vector<int> t;
+  if (d.n_q == kNQs) {
+    if (d.n_rad == 2 && d.nu_max == 2) t = slot_table<2, 2>();
+    else if (d.n_rad == 3 && d.nu_max == 4) t = slot_table<3, 4>();
+    else if (d.n_rad == 4 && d.nu_max == 6) t = slot_table<4, 6>();
+    else if (d.n_rad == 5 && d.nu_max == 8) t = slot_table<5, 8>();
+  }
+  if (t.empty() || static_cast<int>(t.size()) != d.n_mom) return;
+  m->split_tab.ensure(t.size() * sizeof(int), 0);
+  MTP_CUDA(cudaMemcpy(m->split_tab.p, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice));
+}
+
+// The three-kernel mixed pass.  Returns false (nothing launched) when the model's shape has no
+// specialised instantiation, when the outputs are not the step's (FP64 rows, an explicit atom
+// list), or when no moment workspace was given; the caller then uses another kernel.
+bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const SiteOutputs& o, cudaStream_t s) {
+  const DevSchedule& d = m->ds;
+  float* mom_ws = o.mom;
+  if (!mom_ws || !split_wanted(m) || !d.tri_pk || d.n_q != kNQs || d.n_types > 3) return false;
+  if (o.rows || o.atom_list) return false;
+  const bool efs = o.V != nullptr;
+  const bool rows = o.rows_hi != nullptr;
+  if (!efs && !rows) return false;
+  if (efs && (!o.G || !o.Wat)) return false;
+  const int nr = d.n_rad, nu0 = d.nu_max;
+  const bool shape_ok = (nr == 2 && nu0 == 2) || (nr == 3 && nu0 == 4) || (nr == 4 && nu0 == 6) || (nr == 5 && nu0 == 8);
+  if (!shape_ok) return false;
+  SplitArgs P{};
+  P.d = d;
+  P.nb = nb->dn;
+  P.type = b->type;
+  P.n_work = nb->n_atoms;
+  P.o = o;
+  P.mom = mom_ws;
+  P.ldm = split_ldm(d.n_mom);
+  P.slot_comp = m->split_tab.as<int>();
+  P.T = d.n_types;
+  P.CBN = d.n_types * d.n_rad * d.n_q;
+  P.NC = d.n_types * P.CBN;
+  P.NV = padded_nv(d.n_vals);
+  P.c_bytes = (static_cast<size_t>(std::max(P.NC, d.n_coef)) * sizeof(float) + 15) & ~size_t(15);
+  int w = 0;
+  auto take = [&](int n) { const int o2 = w; w += (n + 3) & ~3; return o2; };
+  P.o_fslab = take(d.fslab_words);
+  P.o_fround = take(4 * d.n_fround);
+  P.o_frdst = take(32 * d.n_fround);
+  P.o_rslab = take(d.rslab_words);
+  P.o_rround = take(4 * d.n_rround);
+  P.o_rrval = take(32 * d.n_rround);
+  P.o_seed = take(d.n_vals);
+  P.sched_bytes = static_cast<size_t>(w) * 4;
+  const int nbc = m->tune_split_nb > 0 ? m->tune_split_nb : 2;
+  P.warp_bytes = static_cast<size_t>(2 * nbc * P.NV) * sizeof(float);
+  if (P.c_bytes + P.sched_bytes + P.warp_bytes > 227 * 1024) return false;
+  P.total = P.c_bytes + P.sched_bytes + P.warp_bytes;
+  const int wp = m->tune_split_warps > 0 ? m->tune_split_warps : 8;
+  m->last_fast = true;
+  m->last_split = true;
+  m->last_warps = wp;
+  if (P.n_work == 0) return true;
+  if (nr == 2) launch_split<2, 2>(P, wp, nbc, efs, rows, s);
+  else if (nr == 3) launch_split<3, 4>(P, wp, nbc, efs, rows, s);
+  else if (nr == 4) launch_split<4, 6>(P, wp, nbc, efs, rows, s);
+  else launch_split<5, 8>(P, wp, nbc, efs, rows, s);
+#ifdef MTP_SPLIT_CHECK
+  unsigned long long fault = 0;
+  MTP_CUDA(cudaStreamSynchronize(s));
+  MTP_CUDA(cudaMemcpyFromSymbol(&fault, g_split_fault, sizeof(fault)));
+  if (fault) {
+    const unsigned long long zero = 0;
+    MTP_CUDA(cudaMemcpyToSymbol(g_split_fault, &zero, sizeof(zero)));
+    throw Fail{MTP_ERR_NUMERIC, "split pass: index out of range, check " + std::to_string(fault >> 48) + " index " +
+                                    std::to_string(static_cast<long long>(fault & 0xFFFFFFFFFFFFull))};
+  }
+#endif
+  return true;
+}
+
+}  // namespace mtp

@@ -29,11 +29,18 @@ def test_autotune_keeps_results(api, lev, prec):
     api.mtp_set_active_set(model, torch.tensor(synth.diag_dominant(102, md.m), device="cuda"))
     b = api.Batch(synth.fcc_ternary(seed=103, n=12))
     nb = api.mtp_build_neighbors(model, b)
-    before = {k: v.clone() for k, v in api.mtp_step(model, b, nb, prec).items() if v is not None}
+    # untuned results of each mixed pass (the autotuner may pick either)
+    before = {}
+    for p in ((1, 2) if prec == "mixed" else (0,)):
+        if p:
+            api.mtp_set_mixed_pass(model, p)
+        before[p] = {k: v.clone() for k, v in api.mtp_step(model, b, nb, prec).items() if v is not None}
+    api.mtp_set_mixed_pass(model, "auto")
     w, ms = api.mtp_autotune(model, b, nb, prec)
     assert 1 <= w <= 8 and ms > 0
+    in_use = api.mtp_get_mixed_pass(model)[1] if prec == "mixed" else 0
     after = api.mtp_step(model, b, nb, prec)
-    for k, v in before.items():
+    for k, v in before[in_use].items():
         assert torch.equal(after[k], v), k
 
 
@@ -54,3 +61,16 @@ def test_autotune_of_one_precision_keeps_the_other(api):
     assert api.mtp_get_launch_shape(model) == (fast, fwd, w_fp64)
     api.mtp_autotune(model, b, nb, "mixed")
     assert api.mtp_get_launch_shape(model)[2] == w_fp64
+
+
+def test_measured_peaks_are_plausible(api):
+    """The library's microbenchmarks (the roofline denominators): FP32 FMA between a third of
+    and just above 152 SMs x 128 lanes x 2 flops at 2.07 GHz; FP64 well below FP32; the TF32
+    tensor-core rate between a quarter of and just above its nominal dense figure."""
+    fp32, _ = api.mtp_measure_peak("fp32_fma")
+    fp64, _ = api.mtp_measure_peak("fp64_fma")
+    tf32, _ = api.mtp_measure_peak("tf32_mma")
+    nominal32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    assert nominal32 / 3 < fp32 < nominal32 * 1.05
+    assert 0 < fp64 < fp32
+    assert 1100.0 / 4 < tf32 < 1100.0 * 1.3

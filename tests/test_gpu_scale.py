@@ -68,7 +68,8 @@ def big(api):
     rows = s["b"][[pos_of[int(k)] for k in sample]]
     gamma, am = O.grade(A, rows)
     V = s["V"][[pos_of[int(k)] for k in sample]]
-    return {"outs": outs, "sample": sample, "V": V, "F": F, "gamma": gamma, "argmax": am, "n": len(bnp["type"])}
+    return {"outs": outs, "sample": sample, "V": V, "F": F, "gamma": gamma, "argmax": am, "n": len(bnp["type"]),
+            "rows": rows, "model": model, "b": b, "nb": nb, "md": md, "theta": theta}
 
 
 def test_million_atom_site_energies_on_sampled_atoms(big):
@@ -91,6 +92,60 @@ def test_million_atom_grade_on_sampled_atoms(big):
     assert (big["outs"]["fp64"]["argmax"][k] == big["argmax"]).all()
     g = big["gamma"]
     assert np.all(np.abs(big["outs"]["mixed"]["gamma"][k] - g) <= 1e-4 * np.maximum(1.0, g))
+
+
+@pytest.fixture(scope="module")
+def maxvol_set(api, big):
+    """The benchmark's active set, formed by the oracle: FP64 rows of a 2048-atom companion
+    snapshot (independent displacements), m - n_gauge of them drawn without replacement plus the
+    gauge completion, then MaxVol swaps over all 2048 rows while some |C_ij| > 1.01."""
+    from oracle import active_set as AS
+    md, theta = big["md"], big["theta"]
+    comp = synth.fcc_ternary(seed=444, n=8)
+    crows = O.site_rows(md, theta, comp["type"], O.batch_neighbors(comp, 5.0))
+    D = O.gauge_directions(md, theta)
+    pick = synth.sample_atoms(444, len(comp["type"]), md.m - len(D))
+    A0 = np.vstack([crows[pick], D / np.linalg.norm(D, axis=1, keepdims=True) * np.abs(crows).max()])
+    A, src, n_sw = AS.maxvol(A0, crows, eps=1e-2)
+    active = np.array([pick[j] if src[j] < 0 else src[j] for j in range(len(pick))])
+    return {"A": A, "comp": comp, "active": active, "swaps": n_sw, "crows": crows}
+
+
+def test_million_atom_grade_with_maxvol_active_set(api, big, maxvol_set):
+    """Both GPU paths against the oracle on the sampled atoms, at the MaxVol active set (2-norm
+    condition number about 3e13: the rows of lattice neighborhoods are nearly dependent).  FP64:
+    1e-6 relative (the conditioning of A^-1 limits any FP64 evaluation; 1e-10 holds for the
+    well-conditioned sets of the other tests) and the same argmax; mixed: within its per-atom
+    allowance (grade_floor.py).  Active rows grade 1, and the flag gamma > 2 selects a small
+    fraction of the atoms."""
+    from grade_floor import grade_sensitivity, mixed_grade_bound, mixed_grade_ok
+    A = maxvol_set["A"]
+    model, b, nb, k = big["model"], big["b"], big["nb"], big["sample"]
+    api.mtp_set_active_set(model, torch.tensor(A, device="cuda"))
+    ref, am = O.grade(A, big["rows"])
+    S = grade_sensitivity(A, big["rows"])
+    out = {p: api.mtp_grade(model, b, nb, p, threshold=2.0) for p in ("fp64", "mixed")}
+    g64 = out["fp64"]["gamma"].cpu().numpy()
+    np.testing.assert_allclose(g64[k], ref, rtol=1e-6)
+    assert (out["fp64"]["argmax"].cpu().numpy()[k] == am).all()
+    assert np.all(mixed_grade_ok(out["mixed"]["gamma"].cpu().numpy()[k], ref, S))
+    assert int(out["fp64"]["n_flagged"].item()) < 0.05 * big["n"]
+    # the companion's own neighborhoods: its active rows grade 1
+    comp = api.Batch(maxvol_set["comp"])
+    cnb = api.mtp_build_neighbors(model, comp)
+    ref_c, _ = O.grade(A, maxvol_set["crows"])
+    assert ref_c.max() <= 1.01 + 1e-6                 # MaxVol stopped: no swap gains more than 1 %
+    S_c = grade_sensitivity(A, maxvol_set["crows"])
+    act = maxvol_set["active"]
+    for prec in ("fp64", "mixed"):
+        gc = api.mtp_grade(model, comp, cnb, prec, threshold=2.0)["gamma"].cpu().numpy()
+        if prec == "fp64":
+            np.testing.assert_allclose(gc[act], 1.0, atol=1e-6)
+            np.testing.assert_allclose(gc, ref_c, rtol=1e-6)
+        else:
+            assert np.all(np.abs(gc[act] - 1.0) <= mixed_grade_bound(1.0, S_c[act]))
+            assert np.all(mixed_grade_ok(gc, ref_c, S_c))
+    api.mtp_set_active_set(model, torch.tensor(synth.diag_dominant(8, big["md"].m), device="cuda"))
 
 
 def test_million_atom_invariants(big):
