@@ -304,7 +304,10 @@ def run_ours(args):
     grade = cfg["grade"]
 
     measured = measure_peaks(api) if not args.no_peaks else None
-    bnp = w.inputs(w.input_seed + rank)
+    if args.cells and args.config == "C4":
+        bnp = synth.fcc_ternary(seed=w.input_seed + rank, n=args.cells)   # smaller C4 cells (profiling)
+    else:
+        bnp = w.inputs(w.input_seed + rank)
     desc, theta = w.desc(), w.theta()
     sizes = api.mtp_describe(desc)
     m = sizes["n_params"]
@@ -324,6 +327,9 @@ def run_ours(args):
     nb = api.Neighbors()
     out = None
     api.mtp_build_neighbors(model, batch, nb)
+    api.mtp_set_mixed_pass(model, args.mixed_pass)
+    if args.split_shape:
+        api.mtp_set_split_shape(model, *[int(x) for x in args.split_shape.split(",")])
     # the library's autotuner picks the per-neighborhood kernel's launch shape on this workload
     # (the FP64 kernel keeps its default shape above 10^6 atoms: one FP64 pass there takes seconds)
     tuned = {}
@@ -592,7 +598,8 @@ def run_ours(args):
                                         "and replayed from one CUDA graph"},
         "roofline": roof,
         "roofline_kernels": {k: roof_of(k) for k in per_step if k in work and k != dominant},
-        "mixed_pass": dict(zip(("setting", "in_use", "split_warps", "split_nb"), api.mtp_get_mixed_pass(model))),
+        "mixed_pass": dict(zip(("setting", "in_use", "split_warps", "split_nb"), api.mtp_get_mixed_pass(model)),
+                           requested=args.mixed_pass),
         "measured_peaks": measured, "kernels": kernels, "gpu_launches": launches, "clocks": clk,
         "e2e": e2e,
     }
@@ -790,6 +797,10 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-peaks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (fixed launch sequence)")
+    ap.add_argument("--split-shape", default="", help="warps_pair,nb_contract of the three-kernel pass (no autotune)")
+    ap.add_argument("--cells", type=int, default=0, help="C4 only: n^3 fcc cells instead of 64^3 (profiling)")
+    ap.add_argument("--mixed-pass", default="auto", choices=["auto", "single", "split"],
+                    help="mixed path: the autotuner's choice, the single kernel or the three kernels")
     ap.add_argument("--ref-sample", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":

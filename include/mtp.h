@@ -335,6 +335,12 @@ mtp_status mtp_get_launch_shape(const mtp_model* model, int32_t* warps_fast, int
  * MTP_ERR_UNSUPPORTED for 2 when the shape has no three-kernel pass.  No GPU work. */
 mtp_status mtp_set_mixed_pass(mtp_model* model, int pass);
 
+/* Launch shape of the three-kernel pass (what mtp_autotune sets): warps per block of its
+ * per-pair kernels (4 or 8; 0 = default 8), neighborhoods per warp of its contraction (1 or 2;
+ * 0 = default 1) and schedule words in flight per lane there (2 or 4; 0 = default 2).  Results
+ * do not depend on it.  No GPU work. */
+mtp_status mtp_set_split_shape(mtp_model* model, int warps_pair, int nb_contract, int unroll);
+
 /* The setting above, the pass the next mixed call will run (1 or 2), and the three-kernel
  * pass's tuned shape (warps per block of its per-pair kernels, neighborhoods per warp of its
  * contraction; 0 = default).  HOST outputs, any may be NULL. */

@@ -72,6 +72,7 @@ _SIGS = {
     "mtp_sync": (ctypes.c_int, [_P, _P]),
     "mtp_set_mixed_pass": (ctypes.c_int, [_P, ctypes.c_int]),
     "mtp_get_mixed_pass": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "mtp_set_split_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mtp_measure_peak": (ctypes.c_int, [ctypes.c_int, _P, _P, _P]),
     "mtp_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "mtp_fit_bfgs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _I64, _D, _P, _P, _P]),
@@ -510,6 +511,10 @@ def mtp_set_mixed_pass(model, p):
     """0 automatic, 1 single kernel, 2 three kernels (or the names "auto", "single", "split")."""
     p = {"auto": 0, "single": 1, "split": 2}.get(p, p)
     _check(lib().mtp_set_mixed_pass(model.h, int(p)))
+
+
+def mtp_set_split_shape(model, warps_pair=0, nb_contract=0, unroll=0):
+    _check(lib().mtp_set_split_shape(model.h, int(warps_pair), int(nb_contract), int(unroll)))
 
 
 def mtp_get_mixed_pass(model):

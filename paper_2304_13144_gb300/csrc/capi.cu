@@ -702,16 +702,18 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     }
     // the three-kernel mixed pass, when the model has one: warps per block of its per-pair
     // kernels x neighborhoods per warp of its contraction (results are the same for every shape)
-    int best_sw = 0, best_snb = 0;
+    int best_sw = 0, best_snb = 0, best_sun = 0;
     float best_split = 0.f;
     const int keep_split = md->tune_split;
     md->mixed_pass = keep_pass;
     if (fast && md->split_tab.p && keep_pass != 1) {
       md->tune_split = 1;
       for (int sw : {4, 8})
-        for (int snb : {1, 2}) {
+        for (int sc : {12, 14, 22, 24}) {
+          const int snb = sc / 10, sun = sc % 10;
           md->tune_split_warps = sw;
           md->tune_split_nb = snb;
+          md->tune_split_unroll = sun;
           run();
           if (!md->last_split) continue;
           float t_min = 0.f;
@@ -724,7 +726,7 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
             MTP_CUDA(cudaEventElapsedTime(&t, e0, e1));
             if (rep == 0 || t < t_min) t_min = t;
           }
-          if (best_sw == 0 || t_min < best_split) { best_split = t_min; best_sw = sw; best_snb = snb; }
+          if (best_sw == 0 || t_min < best_split) { best_split = t_min; best_sw = sw; best_snb = snb; best_sun = sun; }
         }
       md->tune_split = keep_split;
     }
@@ -735,6 +737,7 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     if (best_sw > 0) {
       md->tune_split_warps = best_sw;
       md->tune_split_nb = best_snb;
+      md->tune_split_unroll = best_sun;
       const bool split = md->mixed_pass == 2 || best_split < best_ms;
       if (md->mixed_pass == 0) md->tune_split = split ? 1 : 0;
       if (split) best_ms = best_split;
@@ -761,6 +764,18 @@ mtp_status mtp_set_mixed_pass(mtp_model* md, int pass) {
     if (pass < 0 || pass > 2) throw Fail{MTP_ERR_ARG, "pass must be 0 (automatic), 1 (single kernel) or 2 (three kernels)"};
     if (pass == 2 && !md->split_tab.p) throw Fail{MTP_ERR_UNSUPPORTED, "no three-kernel pass for this model's shape"};
     md->mixed_pass = pass;
+  });
+}
+
+mtp_status mtp_set_split_shape(mtp_model* md, int warps_pair, int nb_contract, int unroll) {
+  return guarded([&] {
+    check_model(md);
+    if (warps_pair != 0 && warps_pair != 4 && warps_pair != 8) throw Fail{MTP_ERR_ARG, "warps_pair must be 0, 4 or 8"};
+    if (nb_contract < 0 || nb_contract > 2) throw Fail{MTP_ERR_ARG, "nb_contract must be 0, 1 or 2"};
+    if (unroll != 0 && unroll != 2 && unroll != 4) throw Fail{MTP_ERR_ARG, "unroll must be 0, 2 or 4"};
+    md->tune_split_warps = warps_pair;
+    md->tune_split_nb = nb_contract;
+    md->tune_split_unroll = unroll;
   });
 }
 

@@ -192,6 +192,7 @@ struct mtp_model {
   int tune_split = -1;
   int tune_split_warps = 0;
   int tune_split_nb = 0;
+  int tune_split_unroll = 0;   // words in flight per lane in the contraction (2 or 4; 0 = 2)
   bool last_split = false;
   mtp::DevBuf split_tab;       // slot -> component table of the split pass (uploaded by mtp_load)
   mtp::DevBuf ws_mom;          // moments / their adjoints of the split pass

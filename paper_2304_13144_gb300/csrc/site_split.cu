@@ -261,7 +261,55 @@ __device__ __forceinline__ void copy_words_s(uint32_t* dst, const uint32_t* src,
   for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
+constexpr int kMaxPre = 10;   // moment components per lane held in registers (n_mom <= 320)
+
+// one slab word: a += c v[x] v[y] (forward) or a += c v[x] g[y] (reverse, w = the adjoint array)
 template <int NB, bool INL>
+__device__ __forceinline__ void slab_term(uint32_t wd, const float* coef, float* const (&v)[NB], float* const (&w)[NB],
+                                          float (&a)[NB]) {
+  float c;
+  uint32_t x, y;
+  if constexpr (INL) {
+    c = __uint_as_float(((wd >> 22) << 17) + 0x3F800000u);
+    x = wd & 2047u;
+    y = (wd >> 11) & 2047u;
+  } else {
+    c = coef[wd >> 24];
+    x = wd & 4095u;
+    y = (wd >> 12) & 4095u;
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) a[j] = fmaf(c, v[j][x] * w[j][y], a[j]);
+}
+
+// one round of 32 destination lists (L words per lane, lane stride 32): UNR words in flight
+template <int NB, bool INL, int UNR>
+__device__ __forceinline__ void slab_round(const uint32_t* slab, int L, const float* coef, float* const (&v)[NB],
+                                           float* const (&w)[NB], float (&acc)[NB]) {
+  float a[UNR][NB];
+#pragma unroll
+  for (int u = 0; u < UNR; ++u)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a[u][j] = 0.f;
+  int it = 0;
+  for (; it + UNR <= L; it += UNR) {
+    uint32_t wd[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) wd[u] = slab[32 * (it + u)];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u]);
+  }
+  for (; it < L; ++it) slab_term<NB, INL>(slab[32 * it], coef, v, w, a[0]);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    float t = acc[j];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) t += a[u][j];
+    acc[j] = t;
+  }
+}
+
+template <int NB, bool INL, int UNR>
 __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
@@ -289,41 +337,56 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   // per warp: NB (values, adjoints) array pairs, each adjoint array NV after its values
   float* const wbase = reinterpret_cast<float*>(smem + P.c_bytes + P.sched_bytes + warp * P.warp_bytes);
   for (int k = lane; k < 2 * NB * NV; k += 32) wbase[k] = 0.f;   // the zero slot n_vals stays 0
-  __syncthreads();
+  float* v[NB];
+  float* g[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    v[j] = wbase + 2 * j * NV;
+    g[j] = v[j] + NV;
+  }
   const int T = P.T;
   const int n_mom = d.n_mom;
-  auto decode = [&](uint32_t w, float& c, uint32_t& x, uint32_t& y) {
-    if constexpr (INL) {
-      c = __uint_as_float(((w >> 22) << 17) + 0x3F800000u);
-      x = w & 2047u;
-      y = (w >> 11) & 2047u;
-    } else {
-      c = coef[w >> 24];
-      x = w & 4095u;
-      y = (w >> 12) & 4095u;
+  // this lane's moment slots (the same for every neighborhood) and their value indices
+  int sc[kMaxPre];
+#pragma unroll
+  for (int r = 0; r < kMaxPre; ++r) {
+    const int k = lane + 32 * r;
+    sc[r] = k < n_mom ? P.slot_comp[k] : -1;
+    if (sc[r] >= 0 && !OK(sc[r], NV, 21)) sc[r] = -1;
+  }
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * nwarps * NB;
+  // moments of the next neighborhoods, loaded one iteration ahead (their global latency overlaps
+  // the contraction of the current ones)
+  float pre[NB][kMaxPre];
+  auto fetch = [&](int64_t w0) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const bool live = w0 + j < P.n_work;
+      const float* src = P.mom + (w0 + j) * P.ldm;
+#pragma unroll
+      for (int r = 0; r < kMaxPre; ++r) {
+        const int k = lane + 32 * r;
+        pre[j][r] = (live && sc[r] >= 0 && OK((w0 + j) * P.ldm + k, P.n_work * P.ldm, 22)) ? __ldcs(src + k) : 0.f;
+      }
     }
   };
-  for (int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * NB; w0 < P.n_work;
-       w0 += static_cast<int64_t>(gridDim.x) * nwarps * NB) {
-    float* v[NB];
-    float* g[NB];
+  int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * NB;
+  if (w0 < P.n_work) fetch(w0);
+  __syncthreads();
+  for (; w0 < P.n_work; w0 += stride) {
     int64_t wk[NB];
     bool live[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      v[j] = wbase + 2 * j * NV;
-      g[j] = v[j] + NV;
       wk[j] = w0 + j;
       live[j] = wk[j] < P.n_work;
-      const float* src = P.mom + (live[j] ? wk[j] : w0) * P.ldm;
-      for (int k = lane; k < n_mom; k += 32) {
-        const int sc = P.slot_comp[k];
-        if (OK(sc, NV, 21) && OK((live[j] ? wk[j] : w0) * P.ldm + k, P.n_work * P.ldm, 22))
-          v[j][sc] = live[j] ? __ldcs(src + k) : 0.f;
-      }
+#pragma unroll
+      for (int r = 0; r < kMaxPre; ++r)
+        if (sc[r] >= 0) v[j][sc[r]] = pre[j][r];
     }
+    if (w0 + stride < P.n_work) fetch(w0 + stride);
     __syncwarp();
-    // ---------------- forward contraction ----------------
+    // ---------------- forward contraction (eqs. 5-6) ----------------
     int4 rd_n = d.n_fround > 0 ? s_fround[0] : make_int4(0, 0, 0, 0);
     int dst_n = d.n_fround > 0 ? s_frdst[lane] : -1;
     for (int r = 0; r < d.n_fround; ++r) {
@@ -333,41 +396,14 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
         rd_n = s_fround[r + 1];
         dst_n = s_frdst[32 * (r + 1) + lane];
       }
-      const uint32_t* slab = s_fslab + rd.y + lane;
-      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.fslab_words, 23)) { rd.x = 0; }
-      float a0[NB], a1[NB];
+      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.fslab_words, 23)) rd.x = 0;
+      float acc[NB];
 #pragma unroll
-      for (int j = 0; j < NB; ++j) { a0[j] = 0.f; a1[j] = 0.f; }
-      int it = 0;
-      for (; it + 4 <= rd.x; it += 4) {
-        const uint32_t w0_ = slab[32 * it], w1_ = slab[32 * it + 32], w2_ = slab[32 * it + 64], w3_ = slab[32 * it + 96];
-        float c0, c1, c2, c3;
-        uint32_t x0, y0, x1, y1, x2, y2, x3, y3;
-        decode(w0_, c0, x0, y0);
-        decode(w1_, c1, x1, y1);
-        decode(w2_, c2, x2, y2);
-        decode(w3_, c3, x3, y3);
-        if (!OK(x0, NV, 24) || !OK(y0, NV, 24) || !OK(x1, NV, 24) || !OK(y1, NV, 24) || !OK(x2, NV, 24) ||
-            !OK(y2, NV, 24) || !OK(x3, NV, 24) || !OK(y3, NV, 24)) continue;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          a0[j] = fmaf(c0, v[j][x0] * v[j][y0], a0[j]);
-          a1[j] = fmaf(c1, v[j][x1] * v[j][y1], a1[j]);
-          a0[j] = fmaf(c2, v[j][x2] * v[j][y2], a0[j]);
-          a1[j] = fmaf(c3, v[j][x3] * v[j][y3], a1[j]);
-        }
-      }
-      for (; it < rd.x; ++it) {
-        float c0;
-        uint32_t x0, y0;
-        decode(slab[32 * it], c0, x0, y0);
-        if (!OK(x0, NV, 25) || !OK(y0, NV, 25)) continue;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) a0[j] = fmaf(c0, v[j][x0] * v[j][y0], a0[j]);
-      }
+      for (int j = 0; j < NB; ++j) acc[j] = 0.f;
+      slab_round<NB, INL, UNR>(s_fslab + rd.y + lane, rd.x, coef, v, v, acc);
       if (dst >= 0 && OK(dst, NV, 26)) {
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v[j][dst] = a0[j] + a1[j];
+        for (int j = 0; j < NB; ++j) v[j][dst] = acc[j];
       }
       if (rd.z) __syncwarp();
     }
@@ -384,52 +420,29 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
         if (lane == 0) P.o.V[i] = static_cast<double>(acc) + d.theta_d[P.type[i]];
       }
     }
-    // ---------------- adjoint of the contraction (gather form) ----------------
+    // ---------------- adjoint of the contraction (gather form), seeded with xi ----------------
     rd_n = d.n_rround > 0 ? s_rround[0] : make_int4(0, 0, 0, 0);
     int x_n = d.n_rround > 0 ? s_rrval[lane] : -1;
+    float sd_n = (x_n >= 0 && OK(x_n, d.n_vals, 28)) ? s_seed[x_n] : 0.f;
+    int x_nn = d.n_rround > 1 ? s_rrval[32 + lane] : -1;
     for (int r = 0; r < d.n_rround; ++r) {
       int4 rd = rd_n;
       const int x = x_n;
+      const float sd = sd_n;
       if (r + 1 < d.n_rround) {
         rd_n = s_rround[r + 1];
-        x_n = s_rrval[32 * (r + 1) + lane];
+        x_n = x_nn;
+        sd_n = (x_n >= 0 && OK(x_n, d.n_vals, 28)) ? s_seed[x_n] : 0.f;
       }
-      const float sd = (x >= 0 && OK(x, d.n_vals, 28)) ? s_seed[x] : 0.f;
-      const uint32_t* slab = s_rslab + rd.y + lane;
-      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.rslab_words, 29)) { rd.x = 0; }
-      float a0[NB], a1[NB];
+      if (r + 2 < d.n_rround) x_nn = s_rrval[32 * (r + 2) + lane];
+      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.rslab_words, 29)) rd.x = 0;
+      float acc[NB];
 #pragma unroll
-      for (int j = 0; j < NB; ++j) { a0[j] = sd; a1[j] = 0.f; }
-      int it = 0;
-      for (; it + 4 <= rd.x; it += 4) {
-        const uint32_t w0_ = slab[32 * it], w1_ = slab[32 * it + 32], w2_ = slab[32 * it + 64], w3_ = slab[32 * it + 96];
-        float c0, c1, c2, c3;
-        uint32_t x0, y0, x1, y1, x2, y2, x3, y3;
-        decode(w0_, c0, x0, y0);
-        decode(w1_, c1, x1, y1);
-        decode(w2_, c2, x2, y2);
-        decode(w3_, c3, x3, y3);
-        if (!OK(x0, NV, 30) || !OK(y0, NV, 30) || !OK(x1, NV, 30) || !OK(y1, NV, 30) || !OK(x2, NV, 30) ||
-            !OK(y2, NV, 30) || !OK(x3, NV, 30) || !OK(y3, NV, 30)) continue;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          a0[j] = fmaf(c0, v[j][x0] * g[j][y0], a0[j]);
-          a1[j] = fmaf(c1, v[j][x1] * g[j][y1], a1[j]);
-          a0[j] = fmaf(c2, v[j][x2] * g[j][y2], a0[j]);
-          a1[j] = fmaf(c3, v[j][x3] * g[j][y3], a1[j]);
-        }
-      }
-      for (; it < rd.x; ++it) {
-        float c0;
-        uint32_t x0, y0;
-        decode(slab[32 * it], c0, x0, y0);
-        if (!OK(x0, NV, 31) || !OK(y0, NV, 31)) continue;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) a0[j] = fmaf(c0, v[j][x0] * g[j][y0], a0[j]);
-      }
+      for (int j = 0; j < NB; ++j) acc[j] = sd;
+      slab_round<NB, INL, UNR>(s_rslab + rd.y + lane, rd.x, coef, v, g, acc);
       if (x >= 0 && OK(x, NV, 32)) {
 #pragma unroll
-        for (int j = 0; j < NB; ++j) g[j][x] = a0[j] + a1[j];
+        for (int j = 0; j < NB; ++j) g[j][x] = acc[j];
       }
       if (rd.z) __syncwarp();
     }
@@ -439,8 +452,9 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
     for (int j = 0; j < NB; ++j) {
       if (!live[j]) continue;
       float* dst = P.mom + wk[j] * P.ldm;
-      for (int k = lane; k < n_mom; k += 32)
-        if (OK(P.slot_comp[k], NV, 33) && OK(wk[j] * P.ldm + k, P.n_work * P.ldm, 34)) __stcs(dst + k, g[j][P.slot_comp[k]]);
+#pragma unroll
+      for (int r = 0; r < kMaxPre; ++r)
+        if (sc[r] >= 0 && OK(wk[j] * P.ldm + lane + 32 * r, P.n_work * P.ldm, 34)) __stcs(dst + lane + 32 * r, g[j][sc[r]]);
       const int64_t i = atom_of(P, wk[j]);
       const int64_t rw = P.o.row_pos ? P.o.row_pos[i] : wk[j];
       if (P.o.rows_hi) {
@@ -643,7 +657,7 @@ int num_sms() {
 }
 
 template <int NR, int NU0>
-void launch_split(SplitArgs P, int warps_pair, int nb_contract, bool efs, bool rows, cudaStream_t s) {
+void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool efs, bool rows, cudaStream_t s) {
   constexpr int NQ = kNQs;
   const int nsm = num_sms();
   const int64_t groups = (P.n_work + GPW - 1) / GPW;
@@ -680,12 +694,17 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, bool efs, bool r
       MTP_CUDA(cudaGetLastError());
     };
     (void)smem;
+    auto pick = [&](auto nbc, auto unr) {
+      constexpr int NBc = decltype(nbc)::value, U = decltype(unr)::value;
+      if (inl) launch(k_contract<NBc, true, U>);
+      else launch(k_contract<NBc, false, U>);
+    };
     if (nb_contract == 2) {
-      if (inl) launch(k_contract<2, true>);
-      else launch(k_contract<2, false>);
+      if (unroll == 4) pick(std::integral_constant<int, 2>{}, std::integral_constant<int, 4>{});
+      else pick(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{});
     } else {
-      if (inl) launch(k_contract<1, true>);
-      else launch(k_contract<1, false>);
+      if (unroll == 4) pick(std::integral_constant<int, 1>{}, std::integral_constant<int, 4>{});
+      else pick(std::integral_constant<int, 1>{}, std::integral_constant<int, 2>{});
     }
   }
   // ---- pair adjoint ----
@@ -747,7 +766,7 @@ bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const 
   if (efs && (!o.G || !o.Wat)) return false;
   const int nr = d.n_rad, nu0 = d.nu_max;
   const bool shape_ok = (nr == 2 && nu0 == 2) || (nr == 3 && nu0 == 4) || (nr == 4 && nu0 == 6) || (nr == 5 && nu0 == 8);
-  if (!shape_ok) return false;
+  if (!shape_ok || d.n_mom > 32 * kMaxPre) return false;
   SplitArgs P{};
   P.d = d;
   P.nb = nb->dn;
@@ -772,7 +791,7 @@ bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const 
   P.o_rrval = take(32 * d.n_rround);
   P.o_seed = take(d.n_vals);
   P.sched_bytes = static_cast<size_t>(w) * 4;
-  const int nbc = m->tune_split_nb > 0 ? m->tune_split_nb : 2;
+  const int nbc = m->tune_split_nb > 0 ? m->tune_split_nb : 1;
   P.warp_bytes = static_cast<size_t>(2 * nbc * P.NV) * sizeof(float);
   if (P.c_bytes + P.sched_bytes + P.warp_bytes > 227 * 1024) return false;
   P.total = P.c_bytes + P.sched_bytes + P.warp_bytes;
@@ -781,10 +800,11 @@ bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const 
   m->last_split = true;
   m->last_warps = wp;
   if (P.n_work == 0) return true;
-  if (nr == 2) launch_split<2, 2>(P, wp, nbc, efs, rows, s);
-  else if (nr == 3) launch_split<3, 4>(P, wp, nbc, efs, rows, s);
-  else if (nr == 4) launch_split<4, 6>(P, wp, nbc, efs, rows, s);
-  else launch_split<5, 8>(P, wp, nbc, efs, rows, s);
+  const int unr = m->tune_split_unroll == 4 ? 4 : 2;
+  if (nr == 2) launch_split<2, 2>(P, wp, nbc, unr, efs, rows, s);
+  else if (nr == 3) launch_split<3, 4>(P, wp, nbc, unr, efs, rows, s);
+  else if (nr == 4) launch_split<4, 6>(P, wp, nbc, unr, efs, rows, s);
+  else launch_split<5, 8>(P, wp, nbc, unr, efs, rows, s);
 #ifdef MTP_SPLIT_CHECK
   unsigned long long fault = 0;
   MTP_CUDA(cudaStreamSynchronize(s));
