@@ -38,7 +38,17 @@ using namespace shape;
 constexpr int kNQs = 8;      // radial polynomials of the specialised kernels
 constexpr int LPN = 8;       // lanes per neighborhood in the per-pair kernels
 constexpr int GPW = 32 / LPN;
-constexpr int BATCH = 64;    // pairs staged per neighborhood at a time
+constexpr int BATCH = 64;    // pairs staged per neighborhood at a time (moments)
+constexpr int BATCH_A = 32;  // pairs staged per neighborhood at a time (pair adjoint)
+constexpr int GS = 17;       // floats staged per pair for the radial block: g_mu, Q_b, species (odd)
+
+// shared-memory floats per neighborhood group of the pair-adjoint kernel: dV/dM (ldm rounded up
+// to 32, plus 8) then the radial-block staging; the stride is 8 mod 32 banks, so the four groups'
+// broadcast reads of one component hit four different banks, and with the odd per-pair stride
+// the 32 lanes' staging stores hit 32 different banks
+__host__ __device__ inline int adj_region(int ldm, bool rows) {
+  return ((ldm + 31) & ~31) + 8 + (rows ? BATCH_A * GS : 0);
+}
 
 struct SplitArgs {
   DevSchedule d;
@@ -154,7 +164,7 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
   using Tb = Tab<NR, NU0>;
   using CI = ChunkInfo<NR, NU0>;
   constexpr int NQ = kNQs;
-  constexpr int PS = (3 + NR + 3) & ~3;   // staged floats per pair: x, y, z, f_0 .. f_{NR-1}
+  static_assert(NR <= 5, "the staging holds f_0 .. f_4");
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
   float* ctab = reinterpret_cast<float*>(smem);
@@ -163,7 +173,10 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
     if (OK(T + d.n_lin + k, d.n_params, 1)) ctab[k] = d.theta_f[T + d.n_lin + k];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / LPN, q = lane % LPN;
   const int nwarps = blockDim.x >> 5;
-  float* stg = reinterpret_cast<float*>(smem + P.c_bytes) + (static_cast<size_t>(warp) * GPW + grp) * BATCH * PS;
+  // per group: (x, y, z, f_0) and (f_1 .. f_4) of each staged pair as two float4 arrays; the 8
+  // lanes of a group read 8 consecutive float4 (one conflict-free phase of a 128-bit load)
+  float4* stgA = reinterpret_cast<float4*>(smem + P.c_bytes) + (static_cast<size_t>(warp) * GPW + grp) * 2 * BATCH;
+  float4* stgB = stgA + BATCH;
   __syncthreads();
   const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
   for (int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * GPW; w0 < P.n_work;
@@ -190,7 +203,7 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
       __syncwarp();
       for (int t = q; t < nbt; t += LPN) {
         const int64_t p = p0 + base + t;
-        if (!OK(p, P.nb.n_pairs, 6) || !OK(t * PS + PS - 1, BATCH * PS, 7)) continue;
+        if (!OK(p, P.nb.n_pairs, 6) || !OK(t, BATCH, 7)) continue;
         const float4 r = P.nb.pr32[p];
         const int jj = P.nb.pj[p];
         if (!OK(jj, P.nb.n_atoms, 8)) continue;
@@ -198,10 +211,11 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
         if (!OK(zj, T, 9)) continue;
         float f[NR], df[NR];
         radial<NR, NQ>(r.w, czi + zj * NR * NQ, rmin, rcut, f, df, nullptr);
-        float* e = stg + t * PS;
-        e[0] = r.x; e[1] = r.y; e[2] = r.z;
+        float fe[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int mu = 0; mu < NR; ++mu) e[3 + mu] = f[mu];
+        for (int mu = 0; mu < NR; ++mu) fe[mu] = f[mu];
+        stgA[t] = make_float4(r.x, r.y, r.z, fe[0]);
+        stgB[t] = make_float4(fe[1], fe[2], fe[3], fe[4]);
       }
       __syncwarp();
       static_for<0, Sh::NCHUNK>([&](auto Cc) {
@@ -211,12 +225,13 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
 #pragma unroll
         for (int t = 0; t < 32; ++t) acc[t] = 0.f;
         for (int t = q; t < nbt; t += LPN) {
-          if (!OK(t * PS + PS - 1, BATCH * PS, 10)) continue;
-          const float* e = stg + t * PS;
-          const float x = e[0], y = e[1], z = e[2];
+          if (!OK(t, BATCH, 10)) continue;
+          const float4 ea = stgA[t], eb = stgB[t];
+          const float x = ea.x, y = ea.y, z = ea.z;
+          const float fe[5] = {ea.w, eb.x, eb.y, eb.z, eb.w};
           float f[NR];
 #pragma unroll
-          for (int mu = 0; mu < NR; ++mu) f[mu] = e[3 + mu];
+          for (int mu = 0; mu < NR; ++mu) f[mu] = fe[mu];
           float px[DH + 1], py[DH + 1], pz[DH + 1];
           px[0] = py[0] = pz[0] = 1.f;
 #pragma unroll
@@ -486,7 +501,7 @@ template <int NR, int NU0, bool ROWS>
 __global__ void __launch_bounds__(256) k_adjoint(SplitArgs P) {
   using Sh = Shape<NR, NU0>;
   constexpr int NQ = kNQs;
-  constexpr int GS = (NR + NQ + 1 + 3) & ~3;   // staged per pair for the radial block: g_mu, Q_b, species
+  static_assert(NR + NQ + 1 <= GS, "radial-block staging");
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
   const int T = P.T;
@@ -494,12 +509,9 @@ __global__ void __launch_bounds__(256) k_adjoint(SplitArgs P) {
   for (int k = threadIdx.x; k < P.NC; k += blockDim.x) ctab[k] = d.theta_f[T + d.n_lin + k];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / LPN, q = lane % LPN;
   const int nwarps = blockDim.x >> 5;
-  // per group: dV/dM (ldm + 8 floats: the 8-float skew puts the 4 groups' arrays in distinct
-  // banks, so a broadcast read of one component by all groups is one wavefront), then the
-  // radial-block staging (BATCH x GS)
-  const int gstride = P.ldm + 8 + (ROWS ? BATCH * GS : 0);
+  const int gstride = adj_region(P.ldm, ROWS);
   float* gM = reinterpret_cast<float*>(smem + P.c_bytes) + (static_cast<size_t>(warp) * GPW + grp) * gstride;
-  float* rstg = gM + P.ldm + 8;
+  float* rstg = gM + ((P.ldm + 31) & ~31) + 8;
   __syncthreads();
   const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
   for (int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * GPW; w0 < P.n_work;
@@ -535,16 +547,16 @@ __global__ void __launch_bounds__(256) k_adjoint(SplitArgs P) {
 #pragma unroll
       for (int mu = 0; mu < NR; ++mu) cb[z][mu] = 0.f;
     float* Gout = static_cast<float*>(P.o.G);
-    for (int base = 0; base < np_max; base += BATCH) {
-      const int nbt = min(BATCH, np - base);
+    for (int base = 0; base < np_max; base += BATCH_A) {
+      const int nbt = min(BATCH_A, np - base);
       // every lane of the warp runs the same number of iterations (adjoint_pass has warp-wide
       // __syncwarp fences); lanes without a pair of their own work on a dummy one
-      const int nbt_w = min(BATCH, np_max - base);
+      const int nbt_w = min(BATCH_A, np_max - base);
       for (int t0 = 0; t0 < nbt_w; t0 += LPN) {
         const int t = t0 + q;
         const int64_t p = p0 + base + t;
         bool act = t < nbt;
-        if (act && (!OK(p, P.nb.n_pairs, 45) || (ROWS && !OK(t * GS + GS - 1, BATCH * GS, 46)))) act = false;
+        if (act && (!OK(p, P.nb.n_pairs, 45) || (ROWS && !OK(t * GS + GS - 1, BATCH_A * GS, 46)))) act = false;
         float4 r = make_float4(1.f, 0.f, 0.f, 1.f);
         int zj = 0;
         if (act) {
@@ -588,7 +600,7 @@ __global__ void __launch_bounds__(256) k_adjoint(SplitArgs P) {
         __syncwarp();
         // sum_j g_mu(j) Q_b(r_ij) per neighbor species: lane q takes b = q over the staged pairs
         for (int t = 0; t < nbt; ++t) {
-          if (!OK(t * GS + GS - 1, BATCH * GS, 49)) continue;
+          if (!OK(t * GS + GS - 1, BATCH_A * GS, 49)) continue;
           const float* e = rstg + t * GS;
           const float qb = e[NR + q];
           const int zj = __float_as_int(e[NR + NQ]);
@@ -663,8 +675,7 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool
   const int64_t groups = (P.n_work + GPW - 1) / GPW;
   // ---- moments ----
   {
-    constexpr int PS = (3 + NR + 3) & ~3;
-    const size_t smem = P.c_bytes + static_cast<size_t>(warps_pair) * GPW * BATCH * PS * sizeof(float);
+    const size_t smem = P.c_bytes + static_cast<size_t>(warps_pair) * GPW * 2 * BATCH * sizeof(float4);
     auto kern = k_moments<NR, NU0>;
     MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     const int per = blocks_per_sm(kern, warps_pair * 32, smem);
@@ -709,8 +720,7 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool
   }
   // ---- pair adjoint ----
   if (efs || rows) {
-    constexpr int GS = (NR + NQ + 1 + 3) & ~3;
-    const size_t gstride = static_cast<size_t>(P.ldm + 8 + (rows ? BATCH * GS : 0));
+    const size_t gstride = static_cast<size_t>(adj_region(P.ldm, rows));
     const size_t smem = P.c_bytes + static_cast<size_t>(warps_pair) * GPW * gstride * sizeof(float);
     auto go = [&](auto kern) {
       MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
