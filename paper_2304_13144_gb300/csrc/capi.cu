@@ -191,6 +191,11 @@ void upload_schedule(mtp_model* md) {
   std::vector<uint32_t> fslab, rslab;
   std::vector<int> fr_dst, rr_val;
   std::vector<int> fround, rround;   // 4 ints per round
+  // packed rounds for the three-kernel pass's contraction (same words): a long list may take an
+  // aligned group of 2..32 lanes, each lane an equal share, combined by a butterfly; lane entry =
+  // -1 (idle) or dst | log2(group) << 16 | leader << 20; round = {L, off, end_of_wave, grouped}
+  std::vector<uint32_t> pfslab, prslab;
+  std::vector<int> pfr_dst, prr_val, pfround, prround;
   if (packable) {
     auto ci = [&](double c) { return static_cast<uint32_t>(std::lower_bound(coefs.begin(), coefs.end(), c) - coefs.begin()); };
     for (size_t t = 0; t < S.tri_a.size(); ++t)
@@ -233,6 +238,92 @@ void upload_schedule(mtp_model* md) {
         for (int it = 0; it < L; ++it)
           for (int l = 0; l < 32; ++l) rslab.push_back(it < static_cast<int>(ord[l].size()) ? ord[l][it] : pad);
       }
+    // packed rounds: items of one wave sorted by list length (descending); each round takes the
+    // next items with group sizes g = next power of 2 of ceil(len / L) (aligned, non-increasing)
+    // and the L that minimises (32 L + kRoundCost) per term, kRoundCost being the fixed cost of a
+    // round in slot units
+    auto pack_wave = [&](const std::vector<int>& items, auto&& list_of, std::vector<uint32_t>& slab,
+                         std::vector<int>& lane_item, std::vector<int>& rounds, auto&& bank_a, auto&& bank_b,
+                         auto&& swap) {
+      constexpr double kRoundCost = 300.0;
+      auto np2 = [](int x) { int g = 1; while (g < x) g *= 2; return g; };
+      const int n = static_cast<int>(items.size());
+      int i = 0;
+      while (i < n) {
+        const int len0 = static_cast<int>(list_of(items[i]).size());
+        int bestL = -1, bestj = i + 1;
+        double best_cost = 1e300;
+        for (int g0 = 1; g0 <= 32; g0 *= 2) {
+          const int L = len0 == 0 ? 0 : (len0 + g0 - 1) / g0;
+          int lanes = 0, j = i;
+          long long tot = 0;
+          while (j < n) {
+            const int len = static_cast<int>(list_of(items[j]).size());
+            const int g = (L == 0 || len == 0) ? 1 : np2((len + L - 1) / L);
+            if (L == 0 && len > 0) break;
+            if (lanes + g > 32) break;
+            lanes += g;
+            tot += len;
+            ++j;
+          }
+          if (j == i) continue;
+          const double cost = L == 0 ? 0.0 : (32.0 * L + kRoundCost) / static_cast<double>(tot);
+          if (bestL < 0 || cost < best_cost - 1e-12 || (std::abs(cost - best_cost) <= 1e-12 && j > bestj)) {
+            best_cost = cost; bestL = L; bestj = j;
+          }
+        }
+        const int L = bestL, j = bestj;
+        std::vector<std::vector<uint32_t>> lists(32);
+        std::vector<int> entry(32, -1);
+        bool grouped = false;
+        int lane = 0;
+        for (int k = i; k < j; ++k) {
+          const auto& lst = list_of(items[k]);
+          const int len = static_cast<int>(lst.size());
+          const int g = (L == 0 || len == 0) ? 1 : np2((len + L - 1) / L);
+          int lg = 0;
+          while ((1 << lg) < g) ++lg;
+          if (g > 1) grouped = true;
+          const int chunk = g > 1 ? (len + g - 1) / g : len;
+          for (int q = 0; q < g; ++q) {
+            for (int t = q * chunk; t < std::min(len, (q + 1) * chunk); ++t) lists[lane + q].push_back(lst[t]);
+            entry[lane + q] = items[k] | (lg << 16) | ((q == 0 ? 1 : 0) << 20);
+          }
+          lane += g;
+        }
+        rounds.insert(rounds.end(), {L, static_cast<int>(slab.size()), j == n ? 1 : 0, grouped ? 1 : 0});
+        lane_item.insert(lane_item.end(), entry.begin(), entry.end());
+        auto ord = bank_order(lists, L, bank_a, bank_b, swap);
+        for (int it = 0; it < L; ++it)
+          for (int l = 0; l < 32; ++l) slab.push_back(it < static_cast<int>(ord[l].size()) ? ord[l][it] : pad);
+        i = j;
+      }
+    };
+    {
+      std::vector<std::vector<uint32_t>> flist(nv);
+      for (int x = nm; x < nv; ++x)
+        for (int t = S.dst_ptr[x - nm]; t < S.dst_ptr[x - nm + 1]; ++t) flist[x].push_back(tri_pk[t]);
+      std::vector<std::vector<uint32_t>> rlist(nv);
+      for (int x = 0; x < nv; ++x)
+        for (int u = use_ptr[x]; u < use_ptr[x + 1]; ++u) rlist[x].push_back(use_pk[u]);
+      auto by_len = [&](std::vector<std::vector<uint32_t>>& L_, std::vector<int> items) {
+        std::stable_sort(items.begin(), items.end(), [&](int a, int b) { return L_[a].size() > L_[b].size(); });
+        return items;
+      };
+      const uint32_t gofs = static_cast<uint32_t>(padded_nv(nv));
+      for (int wv = 0; wv + 1 < static_cast<int>(fwave_ptr.size()); ++wv) {
+        std::vector<int> items(fdst.begin() + fwave_ptr[wv], fdst.begin() + fwave_ptr[wv + 1]);
+        pack_wave(by_len(flist, items), [&](int x) -> const std::vector<uint32_t>& { return flist[x]; }, pfslab,
+                  pfr_dst, pfround, [](uint32_t w) { return w & 4095u; }, [](uint32_t w) { return (w >> 12) & 4095u; },
+                  [](uint32_t w) { return (w & 0xff000000u) | ((w & 4095u) << 12) | ((w >> 12) & 4095u); });
+      }
+      for (int wv = 0; wv + 1 < static_cast<int>(rwave_ptr.size()); ++wv) {
+        std::vector<int> items(rval.begin() + rwave_ptr[wv], rval.begin() + rwave_ptr[wv + 1]);
+        pack_wave(by_len(rlist, items), [&](int x) -> const std::vector<uint32_t>& { return rlist[x]; }, prslab,
+                  prr_val, prround, [](uint32_t w) { return w & 4095u; },
+                  [gofs](uint32_t w) { return gofs + ((w >> 12) & 4095u); }, [](uint32_t w) { return w; });
+      }
+    }
   }
   // inline coefficients when every coefficient is m 2^e with m < 128 (as the multinomial
   // weights of the contraction are) and the value indices fit 11 bits with the zero slot
@@ -260,6 +351,8 @@ void upload_schedule(mtp_model* md) {
       };
       for (auto& w : fslab) w = conv(w);
       for (auto& w : rslab) w = conv(w);
+      for (auto& w : pfslab) w = conv(w);
+      for (auto& w : prslab) w = conv(w);
       coef_inline = true;
     }
   }
@@ -277,6 +370,25 @@ void upload_schedule(mtp_model* md) {
     };
     for (uint32_t w : fslab) check_word(w, "forward slab");
     for (uint32_t w : rslab) check_word(w, "reverse slab");
+    for (uint32_t w : pfslab) check_word(w, "packed forward slab");
+    for (uint32_t w : prslab) check_word(w, "packed reverse slab");
+    auto check_packed = [&](const std::vector<int>& rounds, const std::vector<int>& entries, const std::vector<uint32_t>& slab,
+                            int lo, const char* what) {
+      if (entries.size() != 8 * rounds.size()) bad(what);
+      for (size_t r = 0; r < rounds.size(); r += 4) {
+        if (rounds[r] < 0 || rounds[r + 1] < 0 ||
+            static_cast<size_t>(rounds[r + 1]) + 32 * static_cast<size_t>(rounds[r]) > slab.size())
+          bad(what);
+        for (int l = 0; l < 32; ++l) {
+          const int e = entries[8 * r + l];
+          if (e == -1) continue;
+          const int x = e & 0xffff, lg = (e >> 16) & 15;
+          if (x < lo || x >= nv || lg > 5 || (l & ((1 << lg) - 1)) != 0 && ((e >> 20) & 1)) bad(what);
+        }
+      }
+    };
+    check_packed(pfround, pfr_dst, pfslab, nm, "packed forward rounds");
+    check_packed(prround, prr_val, prslab, 0, "packed reverse rounds");
     for (int x : fr_dst)
       if (x != -1 && (x < nm || x >= nv)) bad("forward destinations");
     for (int x : rr_val)
@@ -296,6 +408,8 @@ void upload_schedule(mtp_model* md) {
   const size_t o_tpk = put(blob, tri_pk), o_upk = put(blob, use_pk), o_cf = put(blob, coef_f);
   const size_t o_fs = put(blob, fslab), o_fr = put(blob, fround), o_frd = put(blob, fr_dst), o_rs = put(blob, rslab),
                o_rr = put(blob, rround), o_rrv = put(blob, rr_val);
+  const size_t o_pfs = put(blob, pfslab), o_pfr = put(blob, pfround), o_pfd = put(blob, pfr_dst),
+               o_prs = put(blob, prslab), o_prr = put(blob, prround), o_prv = put(blob, prr_val);
   const size_t o_ci = put(blob, comp_info), o_fwp = put(blob, fwave_ptr), o_fd = put(blob, fdst),
                o_tp = put(blob, S.dst_ptr), o_tab = put(blob, tri_ab), o_tcf = put(blob, tri_cf),
                o_tcd = put(blob, S.tri_c), o_rwp = put(blob, rwave_ptr), o_rv = put(blob, rval),
@@ -341,6 +455,16 @@ void upload_schedule(mtp_model* md) {
   D.n_rround = static_cast<int>(rround.size() / 4);
   D.rslab_words = static_cast<int>(rslab.size());
   D.n_use = static_cast<int>(use_od.size());
+  D.pfslab = reinterpret_cast<const uint32_t*>(base + o_pfs);
+  D.pfround = reinterpret_cast<const int4*>(base + o_pfr);
+  D.pfr_dst = reinterpret_cast<const int*>(base + o_pfd);
+  D.n_pfround = static_cast<int>(pfround.size() / 4);
+  D.pfslab_words = static_cast<int>(pfslab.size());
+  D.prslab = reinterpret_cast<const uint32_t*>(base + o_prs);
+  D.prround = reinterpret_cast<const int4*>(base + o_prr);
+  D.prr_val = reinterpret_cast<const int*>(base + o_prv);
+  D.n_prround = static_cast<int>(prround.size() / 4);
+  D.prslab_words = static_cast<int>(prslab.size());
 }
 
 void upload_theta(mtp_model* md) {

@@ -90,6 +90,17 @@ struct DevSchedule {
   const int4* rround;
   const int* rr_val;        // [n_rround * 32], -1 = idle lane
   int n_rround, rslab_words;
+  // packed rounds of the three-kernel pass's contraction: a long list takes an aligned group of
+  // 2..32 lanes (equal shares, combined by a butterfly); lane entry -1 (idle) or
+  // index | log2(group) << 16 | leader << 20; round = {L, off, end_of_wave, grouped}
+  const uint32_t* pfslab;
+  const int4* pfround;
+  const int* pfr_dst;
+  int n_pfround, pfslab_words;
+  const uint32_t* prslab;
+  const int4* prround;
+  const int* prr_val;
+  int n_prround, prslab_words;
   const double* theta_d;    // [n_params]
   const float* theta_f;
   const double* seed_d;     // [n_vals] sum of xi over basis functions stored at that value

@@ -297,13 +297,15 @@ __device__ __forceinline__ void slab_term(uint32_t wd, const float* coef, float*
   for (int j = 0; j < NB; ++j) a[j] = fmaf(c, v[j][x] * w[j][y], a[j]);
 }
 
-// one round of 32 destination lists (L words per lane, lane stride 32): UNR words in flight
+// one round of 32 destination lists (L words per lane, lane stride 32): UNR words in flight,
+// word it always added to chain it % 2 (the sum is the same for every UNR, bit for bit)
 template <int NB, bool INL, int UNR>
 __device__ __forceinline__ void slab_round(const uint32_t* slab, int L, const float* coef, float* const (&v)[NB],
                                            float* const (&w)[NB], float (&acc)[NB]) {
-  float a[UNR][NB];
+  static_assert(UNR % 2 == 0, "whole pairs of words per iteration");
+  float a[2][NB];
 #pragma unroll
-  for (int u = 0; u < UNR; ++u)
+  for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int j = 0; j < NB; ++j) a[u][j] = 0.f;
   int it = 0;
@@ -312,15 +314,25 @@ __device__ __forceinline__ void slab_round(const uint32_t* slab, int L, const fl
 #pragma unroll
     for (int u = 0; u < UNR; ++u) wd[u] = slab[32 * (it + u)];
 #pragma unroll
-    for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u]);
+    for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u & 1]);
   }
-  for (; it < L; ++it) slab_term<NB, INL>(slab[32 * it], coef, v, w, a[0]);
+  for (; it < L; ++it) slab_term<NB, INL>(slab[32 * it], coef, v, w, a[it & 1]);
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    float t = acc[j];
+  for (int j = 0; j < NB; ++j) acc[j] += a[0][j] + a[1][j];
+}
+
+// partial sums of a list split over an aligned group of 2^lg lanes (lane entry bits 16..19):
+// after the butterfly every lane of the group holds the group's total (idle lanes: garbage)
+template <int NB>
+__device__ __forceinline__ void group_combine(float (&acc)[NB], int ent) {
+  const int g = 1 << ((ent >> 16) & 15);
 #pragma unroll
-    for (int u = 0; u < UNR; ++u) t += a[u][j];
-    acc[j] = t;
+  for (int s = 1; s < 32; s <<= 1) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const float t = __shfl_xor_sync(0xffffffffu, acc[j], s);
+      if (g > s) acc[j] += t;
+    }
   }
 }
 
@@ -333,12 +345,12 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   for (int k = threadIdx.x; k < d.n_coef; k += blockDim.x)
     if (OK(k * 4 + 3, static_cast<long long>(P.c_bytes), 20)) coef[k] = d.coef_f[k];
   uint32_t* sched = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
-  copy_words_s(sched + P.o_fslab, d.fslab, d.fslab_words);
-  copy_words_s(sched + P.o_fround, reinterpret_cast<const uint32_t*>(d.fround), 4 * d.n_fround);
-  copy_words_s(sched + P.o_frdst, reinterpret_cast<const uint32_t*>(d.fr_dst), 32 * d.n_fround);
-  copy_words_s(sched + P.o_rslab, d.rslab, d.rslab_words);
-  copy_words_s(sched + P.o_rround, reinterpret_cast<const uint32_t*>(d.rround), 4 * d.n_rround);
-  copy_words_s(sched + P.o_rrval, reinterpret_cast<const uint32_t*>(d.rr_val), 32 * d.n_rround);
+  copy_words_s(sched + P.o_fslab, d.pfslab, d.pfslab_words);
+  copy_words_s(sched + P.o_fround, reinterpret_cast<const uint32_t*>(d.pfround), 4 * d.n_pfround);
+  copy_words_s(sched + P.o_frdst, reinterpret_cast<const uint32_t*>(d.pfr_dst), 32 * d.n_pfround);
+  copy_words_s(sched + P.o_rslab, d.prslab, d.prslab_words);
+  copy_words_s(sched + P.o_rround, reinterpret_cast<const uint32_t*>(d.prround), 4 * d.n_prround);
+  copy_words_s(sched + P.o_rrval, reinterpret_cast<const uint32_t*>(d.prr_val), 32 * d.n_prround);
   copy_words_s(sched + P.o_seed, reinterpret_cast<const uint32_t*>(d.seed_f), d.n_vals);
   const uint32_t* s_fslab = sched + P.o_fslab;
   const int4* s_fround = reinterpret_cast<const int4*>(sched + P.o_fround);
@@ -402,21 +414,23 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
     if (w0 + stride < P.n_work) fetch(w0 + stride);
     __syncwarp();
     // ---------------- forward contraction (eqs. 5-6) ----------------
-    int4 rd_n = d.n_fround > 0 ? s_fround[0] : make_int4(0, 0, 0, 0);
-    int dst_n = d.n_fround > 0 ? s_frdst[lane] : -1;
-    for (int r = 0; r < d.n_fround; ++r) {
+    int4 rd_n = d.n_pfround > 0 ? s_fround[0] : make_int4(0, 0, 0, 0);
+    int dst_n = d.n_pfround > 0 ? s_frdst[lane] : -1;
+    for (int r = 0; r < d.n_pfround; ++r) {
       int4 rd = rd_n;
-      const int dst = dst_n;
-      if (r + 1 < d.n_fround) {
+      const int ent = dst_n;
+      if (r + 1 < d.n_pfround) {
         rd_n = s_fround[r + 1];
         dst_n = s_frdst[32 * (r + 1) + lane];
       }
-      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.fslab_words, 23)) rd.x = 0;
+      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.pfslab_words, 23)) rd.x = 0;
       float acc[NB];
 #pragma unroll
       for (int j = 0; j < NB; ++j) acc[j] = 0.f;
       slab_round<NB, INL, UNR>(s_fslab + rd.y + lane, rd.x, coef, v, v, acc);
-      if (dst >= 0 && OK(dst, NV, 26)) {
+      if (rd.w) group_combine<NB>(acc, ent);
+      const int dst = ent & 0xffff;
+      if (ent >= 0 && ((ent >> 20) & 1) && OK(dst, NV, 26)) {
 #pragma unroll
         for (int j = 0; j < NB; ++j) v[j][dst] = acc[j];
       }
@@ -436,26 +450,27 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
       }
     }
     // ---------------- adjoint of the contraction (gather form), seeded with xi ----------------
-    rd_n = d.n_rround > 0 ? s_rround[0] : make_int4(0, 0, 0, 0);
-    int x_n = d.n_rround > 0 ? s_rrval[lane] : -1;
-    float sd_n = (x_n >= 0 && OK(x_n, d.n_vals, 28)) ? s_seed[x_n] : 0.f;
-    int x_nn = d.n_rround > 1 ? s_rrval[32 + lane] : -1;
-    for (int r = 0; r < d.n_rround; ++r) {
+    rd_n = d.n_prround > 0 ? s_rround[0] : make_int4(0, 0, 0, 0);
+    int x_n = d.n_prround > 0 ? s_rrval[lane] : -1;
+    int x_nn = d.n_prround > 1 ? s_rrval[32 + lane] : -1;
+    for (int r = 0; r < d.n_prround; ++r) {
       int4 rd = rd_n;
-      const int x = x_n;
-      const float sd = sd_n;
-      if (r + 1 < d.n_rround) {
+      const int ent = x_n;
+      if (r + 1 < d.n_prround) {
         rd_n = s_rround[r + 1];
         x_n = x_nn;
-        sd_n = (x_n >= 0 && OK(x_n, d.n_vals, 28)) ? s_seed[x_n] : 0.f;
       }
-      if (r + 2 < d.n_rround) x_nn = s_rrval[32 * (r + 2) + lane];
-      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.rslab_words, 29)) rd.x = 0;
+      if (r + 2 < d.n_prround) x_nn = s_rrval[32 * (r + 2) + lane];
+      const int x = ent & 0xffff;
+      const bool lead = ent >= 0 && ((ent >> 20) & 1);
+      const float sd = (lead && OK(x, d.n_vals, 28)) ? s_seed[x] : 0.f;
+      if (!OK(rd.y + 32 * (rd.x > 0 ? rd.x - 1 : 0) + 31, d.prslab_words, 29)) rd.x = 0;
       float acc[NB];
 #pragma unroll
       for (int j = 0; j < NB; ++j) acc[j] = sd;
       slab_round<NB, INL, UNR>(s_rslab + rd.y + lane, rd.x, coef, v, g, acc);
-      if (x >= 0 && OK(x, NV, 32)) {
+      if (rd.w) group_combine<NB>(acc, ent);
+      if (lead && OK(x, NV, 32)) {
 #pragma unroll
         for (int j = 0; j < NB; ++j) g[j][x] = acc[j];
       }
@@ -793,12 +808,12 @@ bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const 
   P.c_bytes = (static_cast<size_t>(std::max(P.NC, d.n_coef)) * sizeof(float) + 15) & ~size_t(15);
   int w = 0;
   auto take = [&](int n) { const int o2 = w; w += (n + 3) & ~3; return o2; };
-  P.o_fslab = take(d.fslab_words);
-  P.o_fround = take(4 * d.n_fround);
-  P.o_frdst = take(32 * d.n_fround);
-  P.o_rslab = take(d.rslab_words);
-  P.o_rround = take(4 * d.n_rround);
-  P.o_rrval = take(32 * d.n_rround);
+  P.o_fslab = take(d.pfslab_words);
+  P.o_fround = take(4 * d.n_pfround);
+  P.o_frdst = take(32 * d.n_pfround);
+  P.o_rslab = take(d.prslab_words);
+  P.o_rround = take(4 * d.n_prround);
+  P.o_rrval = take(32 * d.n_prround);
   P.o_seed = take(d.n_vals);
   P.sched_bytes = static_cast<size_t>(w) * 4;
   const int nbc = m->tune_split_nb > 0 ? m->tune_split_nb : 1;
