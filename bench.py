@@ -560,10 +560,18 @@ def run_ours(args):
         return {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": measured_traffic(name, N, args.config), "peak_source": src,
                 "ms_per_launch": t * 1e3}
-    top = {k: v for k, v in per_step.items() if k not in split_names}
+    # the neighbor build's regions are one pass as well: HBM-bound, 28 B read per atom (positions,
+    # species) and 29 B written per pair (j, image, r_ij, reverse index, scanned bin)
+    nbr_names = [k for k in per_step if k.startswith("neighbors_")]
+    if nbr_names:
+        per_step["neighbor_build"] = (sum(per_step[k][0] for k in nbr_names), 1.0)
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        work["neighbor_build"] = ("hbm", (28.0 * N + 29.0 * n_pairs) / 1e9, hbm, "GB/s",
+                                  f"{peaks_kind} HBM copy bandwidth")
+    top = {k: v for k, v in per_step.items() if k not in split_names and k not in nbr_names}
     dominant = max(top, key=lambda k: top[k][0])
     roof = roof_of(dominant)
-    per_kernel_only = {k: v for k, v in per_step.items() if k != "site_pass"}
+    per_kernel_only = {k: v for k, v in per_step.items() if k not in ("site_pass", "neighbor_build")}
     total_ms = sum(v[0] for v in per_kernel_only.values())
     kernels = {k: {"ms_per_step": round(v[0], 4), "launches_per_step": v[1], "share": round(v[0] / total_ms, 4)}
                for k, v in sorted(per_kernel_only.items(), key=lambda kv: -kv[1][0])}
@@ -597,7 +605,7 @@ def run_ours(args):
                                 "note": "E/F/W [+ grade + flag] on an unchanged configuration, no rebuild; eager "
                                         "and replayed from one CUDA graph"},
         "roofline": roof,
-        "roofline_kernels": {k: roof_of(k) for k in per_step if k in work and k != dominant},
+        "roofline_kernels": {k: roof_of(k) for k in per_step if k in work and k != dominant and roof_of(k)},
         "mixed_pass": dict(zip(("setting", "in_use", "split_warps", "split_nb"), api.mtp_get_mixed_pass(model)),
                            requested=args.mixed_pass),
         "measured_peaks": measured, "kernels": kernels, "gpu_launches": launches, "clocks": clk,
