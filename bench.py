@@ -62,12 +62,13 @@ COMPANION = {"seed": 444, "cells": 8, "eps": 1e-2}
 # than L2); the traffic grows with the atom count, so a launch over N atoms moves bytes * N / atoms.
 # Reported only while the kernel source is the one that was captured (same SHA-1).
 MEASURED_TRAFFIC = {
-    "site_efs_rows": {"source": "paper_2304_13144_gb300/csrc/site_fast.cu",
-                      "sha1": "169ae7b082683549d6c43bd8e44e670cf6108e25",
-                      "atoms": 131072, "bytes": 119990016 + 725012480},
+    # the three kernels of the split per-neighborhood pass (k_moments + k_contract + k_adjoint)
+    "site_pass": {"source": "paper_2304_13144_gb300/csrc/site_split.cu",
+                  "sha1": "40888aa8d9f22390c28f669112406c36949a519d",
+                  "atoms": 131072, "bytes": (119737088 + 103470336) + (163433984 + 401169152) + (294975488 + 422897408)},
     "grade_tc_tf32x3": {"source": "paper_2304_13144_gb300/csrc/grade_tc.cu",
-                        "sha1": "edc8f658b225b15351d41bea8a0a3621a776d4a4",
-                        "atoms": 131072, "bytes": 708309248 + 2733312},
+                        "sha1": "62e17e87b10aee78ab8b421d2404bd3a45d54efa",
+                        "atoms": 131072, "bytes": 507654656 + 2607872},
 }
 
 
