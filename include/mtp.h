@@ -158,6 +158,11 @@ mtp_status mtp_nbr_size(const mtp_nbr* nbr, int64_t* n_atoms, int64_t* n_pairs);
 mtp_status mtp_nbr_export(const mtp_nbr* nbr, const mtp_batch* batch, int64_t* off, int32_t* j,
                           int32_t* image, double* r, void* stream);
 
+/* Copy the reverse-pair index to DEVICE rev[n_pairs]: rev[p] is the position of (j -> i, -n) for
+ * pair p = (i -> j, n), so rev[rev[p]] = p (the force gather F_i = sum_p (G_p - G_rev(p)) reads
+ * it).  MTP_ERR_ARG on a null list or a null rev with pairs present. */
+mtp_status mtp_nbr_reverse(const mtp_nbr* nbr, int32_t* rev, void* stream);
+
 /* ---------------------------------------------------------------------------------- */
 /* Hot path                                                                           */
 /* ---------------------------------------------------------------------------------- */

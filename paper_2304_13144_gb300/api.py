@@ -87,6 +87,7 @@ _SIGS = {
     "mtp_free_nbr": (None, [_P]),
     "mtp_nbr_size": (ctypes.c_int, [_P, _P, _P]),
     "mtp_nbr_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "mtp_nbr_reverse": (ctypes.c_int, [_P, _P, _P]),
     "mtp_energy_forces_stress": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "mtp_energy_forces_stress_atoms": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "mtp_energy_forces_stress_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
@@ -309,15 +310,26 @@ def mtp_build_neighbors(model: Model, batch: Batch, nbr: Neighbors | None = None
     return nbr
 
 
-def mtp_nbr_export(nbr: Neighbors, batch: Batch, stream=None):
+def mtp_nbr_export(nbr: Neighbors, batch: Batch, want_r=True, stream=None):
     na, npairs = nbr.size()
     off = torch.empty(na + 1, dtype=torch.int64, device="cuda")
     j = torch.empty(max(npairs, 1), dtype=torch.int32, device="cuda")
     img = torch.empty((max(npairs, 1), 3), dtype=torch.int32, device="cuda")
-    r = torch.empty((max(npairs, 1), 3), dtype=torch.float64, device="cuda")
-    _check(lib().mtp_nbr_export(nbr.h, ctypes.byref(batch.c), _ptr(off), _ptr(j), _ptr(img), _ptr(r),
-                                _stream(stream)))
-    return {"off": off, "j": j[:npairs], "img": img[:npairs], "r": r[:npairs]}
+    r = torch.empty((max(npairs, 1), 3), dtype=torch.float64, device="cuda") if want_r else None
+    _check(lib().mtp_nbr_export(nbr.h, ctypes.byref(batch.c), _ptr(off), _ptr(j), _ptr(img),
+                                _ptr(r) if want_r else None, _stream(stream)))
+    out = {"off": off, "j": j[:npairs], "img": img[:npairs]}
+    if want_r:
+        out["r"] = r[:npairs]
+    return out
+
+
+def mtp_nbr_reverse(nbr: Neighbors, stream=None):
+    """rev[p]: position of the reverse pair (j -> i, -n) of pair p = (i -> j, n)."""
+    _, npairs = nbr.size()
+    rev = torch.empty(max(npairs, 1), dtype=torch.int32, device="cuda")
+    _check(lib().mtp_nbr_reverse(nbr.h, _ptr(rev), _stream(stream)))
+    return rev[:npairs]
 
 
 def _prec(p):

@@ -1105,6 +1105,15 @@ mtp_status mtp_nbr_size(const mtp_nbr* nb, int64_t* n_atoms, int64_t* n_pairs) {
   });
 }
 
+mtp_status mtp_nbr_reverse(const mtp_nbr* nb, int32_t* rev, void* stream) {
+  return guarded([&] {
+    if (!nb) throw Fail{MTP_ERR_ARG, "null neighbor list"};
+    if (nb->n_pairs == 0) return;
+    if (!rev) throw Fail{MTP_ERR_ARG, "null rev"};
+    MTP_CUDA(cudaMemcpyAsync(rev, nb->prev.p, nb->n_pairs * sizeof(int32_t), cudaMemcpyDeviceToDevice, as_stream(stream)));
+  });
+}
+
 mtp_status mtp_nbr_export(const mtp_nbr* nb, const mtp_batch* b, int64_t* off, int32_t* j, int32_t* image, double* r,
                           void* stream) {
   return guarded([&] {

@@ -32,7 +32,7 @@ struct Fail {
 
 // device error flag bits
 enum : unsigned { ERRF_GEOMETRY = 1u, ERRF_SPECIES = 2u, ERRF_CAPACITY = 4u, ERRF_NONFINITE = 8u,
-                  ERRF_REVERSE = 16u };
+                  ERRF_REVERSE = 16u, ERRF_REVPEND = 32u };
 
 // ------------------------------------------------------------------------------------
 // device buffer owned by a handle (stream-ordered allocation, grows only)
@@ -214,7 +214,7 @@ struct mtp_nbr {
   int64_t n_atoms = 0, n_pairs = 0, n_cfg = 0;
   mtp::DevNbr dn{};
   mtp::DevBuf off, pj, pimg, prev, pr32, atom_cfg;
-  mtp::DevBuf segs;   // per-atom segment starts of the scanned bins (neighbors.cu)
+  mtp::DevBuf segs;   // per scanned bin and atom: accepted slots and pairs before the bin (neighbors.cu)
   mtp::DevBuf masks;  // per-atom accepted-candidate bits of the count pass (neighbors.cu)
   mtp::DevBuf bins, plan, shifts, wrap, scratch, counts;
   std::vector<mtp::CfgPlan> plans;

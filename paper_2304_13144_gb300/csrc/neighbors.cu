@@ -4,11 +4,17 @@
 //      count / scan / scatter, then sort each bin by atom index (deterministic order);
 //   2. per atom, visit the bins within +-ceil(R_cut nb / h) along each axis (periodic axes
 //      wrap and carry an image shift); count accepted pairs, scan to CSR, fill;
-//   3. reverse-pair index: pair (i -> j, n) is matched with (j -> i, -n).
+//   3. reverse-pair index: pair (i -> j, n) is matched with (j -> i, -n).  The decision is
+//      symmetric (below) and the bin scan order point-symmetric, so when the count pass records,
+//      per atom and scanned bin, the accepted slots and the pairs before that bin, the fill pass
+//      computes each pair's reverse index directly; a search of j's list is the fallback (atoms
+//      past slot 31 of their bin, or cells that scan more than 32 bins).
 // Pair vectors are formed in double-single arithmetic (error-free TwoSum of the FP32 halves of
 // the wrapped positions and of the image shift), so the FP32 copy is the correctly rounded
 // r_ij without any FP64 arithmetic on the hot path; the rare pairs within a relative 4e-6 of
-// the cut-off are decided by an FP64 recomputation of r_ij = (x_j + n.H) - x_i.
+// the cut-off are decided by an FP64 recomputation of r_ij = (x_j + n.H) - x_i, always formed
+// from the same end of the pair (the lower atom index, or the image with a positive leading
+// component), so (i -> j, n) and (j -> i, -n) get bitwise the same |r|^2 and the same decision.
 #include <cub/cub.cuh>
 #include <cuda_runtime.h>
 
@@ -61,9 +67,9 @@ struct NbrArgs {
   int* pimg;
   float4* pr32;
   int* prev;
-  uint16_t* seg;         // [n_atoms x kSegStride] start of each scanned bin's pairs in the atom's
-                         // list (relative), or null when a configuration scans more bins
-  uint8_t* pq;           // per pair: index of the scanned bin it was found in (with seg)
+  uint2* rv;             // [scanned bin q x n_atoms], by bin-order position t: .x = accepted bits of
+                         // the bin's first 32 slots, .y = the atom's pairs before bin q (count
+                         // pass writes, fill reads); null when a configuration scans > 32 bins
   uint32_t* mask;        // [kMaskWords x n_atoms] accepted bits of the first kMaskBits candidates
                          // in scan order, by bin-order position (count pass writes, fill reads)
   unsigned* err;
@@ -176,12 +182,16 @@ __device__ __forceinline__ int decide(const NbrArgs& A, const DevCfg& C, int64_t
   const int m2 = n2 - unpack_img(wj, 2) + unpack_img(wi, 2);
   bool accept;
   if (fabsf(d2 - C.rc2f) <= 4e-6f * C.rc2f || d2 < 1e-10f) {
+    // formed from the canonical end: (x_b + s m.H) - x_a with (a, b, s) = (i, j, +1) or (j, i, -1);
+    // (-m).H is the exact negation of m.H, so both ends give the same rounded |r|^2
+    const bool flip = j < i || (j == i && (m0 < 0 || (m0 == 0 && (m1 < 0 || (m1 == 0 && m2 < 0)))));
+    const long long ia = flip ? j : i, ib = flip ? i : j;
+    const double sg = flip ? -1.0 : 1.0;
     double rr[3];
     for (int c = 0; c < 3; ++c) {
-      const double sh64 = __dadd_rn(__dadd_rn(__dmul_rn(static_cast<double>(m0), C.H[0 * 3 + c]),
-                                              __dmul_rn(static_cast<double>(m1), C.H[1 * 3 + c])),
-                                    __dmul_rn(static_cast<double>(m2), C.H[2 * 3 + c]));
-      rr[c] = __dsub_rn(__dadd_rn(A.pos[3 * j + c], sh64), A.pos[3 * i + c]);
+      const double sh64 = __dadd_rn(__dadd_rn(__dmul_rn(sg * m0, C.H[0 * 3 + c]), __dmul_rn(sg * m1, C.H[1 * 3 + c])),
+                                    __dmul_rn(sg * m2, C.H[2 * 3 + c]));
+      rr[c] = __dsub_rn(__dadd_rn(A.pos[3 * ib + c], sh64), A.pos[3 * ia + c]);
     }
     const double d64 = __dadd_rn(__dadd_rn(__dmul_rn(rr[0], rr[0]), __dmul_rn(rr[1], rr[1])), __dmul_rn(rr[2], rr[2]));
     if (d64 < 1e-16) { atomicOr(A.err, ERRF_GEOMETRY); return 0; }
@@ -195,7 +205,7 @@ __device__ __forceinline__ int decide(const NbrArgs& A, const DevCfg& C, int64_t
   return 1;
 }
 
-constexpr int kSegStride = 28;   // segment starts per atom: up to 27 scanned bins, then the end
+constexpr int kWarpScan = 32;    // the warp fill and the reverse record: at most 32 scanned bins
 constexpr int kMaskWords = 16;   // accepted-candidate bits per atom recorded by the count pass
 constexpr int kMaskBits = 32 * kMaskWords;
 
@@ -217,12 +227,8 @@ __global__ void __launch_bounds__(128, 10) k_pairs(NbrArgs A) {
   long long count = 0;
   int cand = 0;          // candidate index in scan order (the self candidate included)
   uint32_t mword = 0;    // count pass: accepted bits of the current mask word
-  // segment starts: bins are scanned in increasing q = ((d0 + kb0) w1 + (d1 + kb1)) w2 + (d2 + kb2);
-  // skipped bins get empty segments
-  uint16_t* seg = (FILL && A.seg) ? A.seg + i * kSegStride : nullptr;
+  // bins are scanned in increasing q = ((d0 + kb0) w1 + (d1 + kb1)) w2 + (d2 + kb2)
   const int w1 = 2 * C.kb[1] + 1, w2 = 2 * C.kb[2] + 1;
-  const int n_scan = (2 * C.kb[0] + 1) * w1 * w2;
-  int q_next = 0;
   for (int d0 = -C.kb[0]; d0 <= C.kb[0]; ++d0) {
     int t0 = b0 + d0, n0 = 0;
     if (C.pbc[0]) {
@@ -245,8 +251,6 @@ __global__ void __launch_bounds__(128, 10) k_pairs(NbrArgs A) {
           continue;
         }
         const int q = ((d0 + C.kb[0]) * w1 + (d1 + C.kb[1])) * w2 + (d2 + C.kb[2]);
-        if (seg)
-          for (; q_next <= q; ++q_next) seg[q_next] = static_cast<uint16_t>(count);
         const long long tb = C.bin_base + (static_cast<long long>(t0) * C.nb[1] + t1) * C.nb[2] + t2;
         const long long s0 = A.bin_start[tb], s1 = A.bin_start[tb + 1];
         // candidate s of this bin: 1 if (i -> j, n) is a pair (written out in the fill pass)
@@ -261,7 +265,6 @@ __global__ void __launch_bounds__(128, 10) k_pairs(NbrArgs A) {
             A.pj[out] = j;
             A.pimg[out] = img;
             A.pr32[out] = r;
-            if (seg) A.pq[out] = static_cast<uint8_t>(q);
             ++out;
           }
           ++count;
@@ -284,6 +287,8 @@ __global__ void __launch_bounds__(128, 10) k_pairs(NbrArgs A) {
             cand += span;
           }
         }
+        const unsigned before = static_cast<unsigned>(count);
+        uint32_t slots = 0;   // count pass: accepted bits of this bin's first 32 slots
         for (; s < s1; ++s, ++cand) {
           const int acc = test(s);
           if (!FILL && A.mask && cand < kMaskBits) {
@@ -293,23 +298,28 @@ __global__ void __launch_bounds__(128, 10) k_pairs(NbrArgs A) {
               mword = 0;
             }
           }
+          if (!FILL && s - s0 < 32) slots |= static_cast<uint32_t>(acc) << (s - s0);
         }
+        if (!FILL && A.rv) A.rv[static_cast<long long>(q) * A.n_atoms + t] = make_uint2(slots, before);
       }
     }
   }
-  if (seg)
-    for (; q_next <= n_scan; ++q_next) seg[q_next] = static_cast<uint16_t>(count);
   if (!FILL && A.mask && cand < kMaskBits && (cand & 31) != 0)
     A.mask[static_cast<long long>(cand >> 5) * A.n_atoms + t] = mword;
   if (!FILL) A.cnt[i] = count;
   else if (count != out_end - A.off[i]) atomicOr(A.err, ERRF_CAPACITY);
 }
 
-// Fill pass with one warp per atom (bin order), for configurations that scan at most 27 bins:
+// Fill pass with one warp per atom (bin order), for configurations that scan at most 32 bins:
 // lane q owns scanned bin q (its first binned atom, size, image and first candidate index), the
 // count pass's accepted bits are located by prefix popcounts, and lane k forms the atom's k-th
 // pair, so consecutive lanes write consecutive slots.  Candidates past the recorded bits are
 // decided again, 32 at a time, and compacted by ballot.
+// Reverse index: pair (i -> j) found in i's scanned bin q at j's binned position t_j is found
+// from j in j's mirror bin n_scan - 1 - q (the scan order is point-symmetric) at i's slot in
+// its own bin, so its place in j's list is off[j] + (j's pairs before that bin) + (j's accepted
+// slots of that bin below i's slot), all recorded by the count pass.  Atoms past slot 31 of
+// their bin leave -1 and ERRF_REVPEND for the search pass.
 __device__ __forceinline__ int nth_set_bit(uint32_t m, int rem) {   // position of set bit #rem (0-based)
   int pos = 0;
 #pragma unroll
@@ -333,6 +343,7 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(NbrArgs A) {
   const long long out0 = A.off[i], out1 = A.off[i + 1];
   const int w1 = 2 * C.kb[1] + 1, w2 = 2 * C.kb[2] + 1;
   const int n_scan = (2 * C.kb[0] + 1) * w1 * w2;
+  const int slot_i = static_cast<int>(t - A.bin_start[A.atom_bin[i]]);   // i's slot in its bin
   // scanned bin of this lane (same order as k_pairs): first binned atom, size, image
   int n[3] = {0, 0, 0};
   long long s0 = 0;
@@ -392,23 +403,33 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(NbrArgs A) {
   const int nmask = __shfl_sync(full, wpre, 31);
   wpre -= __popc(word);
   // decide candidate c of scanned bin q again (every lane takes part in the shuffles)
-  auto form = [&](int c, int q, bool act, int& j, int& img, float4& r) -> int {
+  auto form = [&](int c, int q, bool act, int& j, int& img, float4& r, long long& sidx) -> int {
     const long long sb = __shfl_sync(full, s0, q);
     const int cq = __shfl_sync(full, cst0, q);
     const int n0 = __shfl_sync(full, n[0], q), n1 = __shfl_sync(full, n[1], q), n2 = __shfl_sync(full, n[2], q);
     if (!act) return 0;
-    const long long sidx = sb + (c - cq);
+    sidx = sb + (c - cq);
     const float4 xj_h = A.bph[sidx];
     j = __float_as_int(xj_h.w);
     if (j == static_cast<int>(i) && n0 == 0 && n1 == 0 && n2 == 0) return 0;
     return decide(A, C, i, j, xi_h, xi_l, xj_h, A.bpl[sidx], n0, n1, n2, r, img);
   };
-  auto put = [&](long long o, int j, int img, const float4& r, int q) {
+  auto put = [&](long long o, int j, int img, const float4& r, int q, long long tj) {
     if (o >= out1) return;
     A.pj[o] = j;
     A.pimg[o] = img;
     A.pr32[o] = r;
-    if (A.pq) A.pq[o] = static_cast<uint8_t>(q);
+    int rev = -1;
+    if (slot_i < 32) {
+      const uint2 e = A.rv[static_cast<long long>(n_scan - 1 - q) * A.n_atoms + tj];
+      const long long oj = A.off[j], oj1 = A.off[j + 1];
+      const long long pr = oj + e.y + __popc(e.x & ((1u << slot_i) - 1u));
+      if (pr < oj1) rev = static_cast<int>(pr);
+      else atomicOr(A.err, ERRF_REVERSE);   // j's record disagrees with its list
+    } else {
+      atomicOr(A.err, ERRF_REVPEND);
+    }
+    A.prev[o] = rev;
   };
   // accepted candidates among the recorded bits: lane k forms the atom's k-th pair
   for (int kb = 0; kb < nmask; kb += 32) {
@@ -425,42 +446,31 @@ __global__ void __launch_bounds__(256, 4) k_fill_warp(NbrArgs A) {
     const int q = bin_of(c);
     int j = 0, img = 0;
     float4 r;
-    if (form(c, q, act, j, img, r)) put(out0 + k, j, img, r, q);
+    long long tj = 0;
+    if (form(c, q, act, j, img, r, tj)) put(out0 + k, j, img, r, q, tj);
     else if (act) atomicOr(A.err, ERRF_CAPACITY);   // the replay disagrees with the count
   }
   long long written = nmask;
-  // pairs before each scanned bin (segment starts): the recorded part ...
-  const int cseg = lane < n_scan ? cst0 : ctot;   // lane n_scan: the end of the list
-  int seg_v;
-  {
-    const int cm = min(cseg, nbits);
-    const int w = min(cm >> 5, 31);
-    const int wp = __shfl_sync(full, wpre, w);
-    const uint32_t ww = __shfl_sync(full, word, w);
-    seg_v = (cm >> 5) >= kMaskWords ? nmask : wp + __popc(ww & ((1u << (cm & 31)) - 1u));
-  }
-  // ... and candidates past the recorded bits, decided again and compacted in scan order
+  // candidates past the recorded bits, decided again and compacted in scan order
   for (int cb = kMaskBits; cb < ctot; cb += 32) {
     const int c = cb + lane;
     const bool act = c < ctot;
     const int q = bin_of(act ? c : cb);
     int j = 0, img = 0;
     float4 r;
-    const int acc = form(c, q, act, j, img, r);
+    long long tj = 0;
+    const int acc = form(c, q, act, j, img, r, tj);
     const unsigned bal = __ballot_sync(full, acc != 0);
-    if (acc) put(out0 + written + __popc(bal & ((1u << lane) - 1u)), j, img, r, q);
-    const int lim = cseg - cb;   // this round's candidates before the lane's segment start
-    if (lim > 0) seg_v += __popc(bal & (lim >= 32 ? full : ((1u << lim) - 1u)));
+    if (acc) put(out0 + written + __popc(bal & ((1u << lane) - 1u)), j, img, r, q, tj);
     written += __popc(bal);
   }
-  if (A.seg && lane <= n_scan) A.seg[i * kSegStride + lane] = static_cast<uint16_t>(seg_v);
   if (lane == 0 && written != out1 - out0) atomicOr(A.err, ERRF_CAPACITY);
 }
 
-// prev[p] = index of the reverse pair (j -> i, -image) of pair p = (i -> j, image): one warp
-// per atom i (its pairs over the lanes).  The bin scan order is point-symmetric: a pair found
-// in i's q-th scanned bin is found from j in j's (n_scan - 1 - q)-th, so with segment starts
-// only that segment of j's list is searched (the whole list otherwise, or as a fallback).
+// prev[p] = index of the reverse pair (j -> i, -image) of pair p = (i -> j, image), by a search
+// of j's list: one warp per atom i (its pairs over the lanes).  MISSING: only the pairs the fill
+// pass left at -1.
+template <bool MISSING>
 __global__ void k_reverse(NbrArgs A) {
   const int lane = threadIdx.x & 31;
   const long long wpb = blockDim.x >> 5;
@@ -468,6 +478,7 @@ __global__ void k_reverse(NbrArgs A) {
   for (long long i = blockIdx.x * wpb + (threadIdx.x >> 5); i < A.n_atoms; i += nw) {
     const long long p1 = A.off[i + 1];
     for (long long p = A.off[i] + lane; p < p1; p += 32) {
+      if (MISSING && A.prev[p] >= 0) continue;
       const int j = A.pj[p];
       if (j < 0 || j >= A.n_atoms) {   // a list that disagrees with its count
         atomicOr(A.err, ERRF_REVERSE);
@@ -477,22 +488,9 @@ __global__ void k_reverse(NbrArgs A) {
       const int img = A.pimg[p];
       const int want = pack_img(-unpack_img(img, 0), -unpack_img(img, 1), -unpack_img(img, 2));
       int found = -1;
-      const long long oj = A.off[j];
-      if (A.seg) {
-        const DevCfg& C = A.cfg[A.atom_cfg[i]];
-        const int n_scan = (2 * C.kb[0] + 1) * (2 * C.kb[1] + 1) * (2 * C.kb[2] + 1);
-        const int qm = n_scan - 1 - min(static_cast<int>(A.pq[p]), n_scan - 1);
-        const uint16_t* sj = A.seg + static_cast<long long>(j) * kSegStride;
-        const long long oj1 = A.off[j + 1];
-        const long long e1 = min(oj + sj[qm + 1], oj1);
-        for (long long q = min(oj + sj[qm], oj1); q < e1; ++q)
-          if (A.pj[q] == static_cast<int>(i) && A.pimg[q] == want) { found = static_cast<int>(q); break; }
-      }
-      if (found < 0) {
-        const long long q1 = A.off[j + 1];
-        for (long long q = oj; q < q1; ++q)
-          if (A.pj[q] == static_cast<int>(i) && A.pimg[q] == want) { found = static_cast<int>(q); break; }
-      }
+      const long long q1 = A.off[j + 1];
+      for (long long q = A.off[j]; q < q1; ++q)
+        if (A.pj[q] == static_cast<int>(i) && A.pimg[q] == want) { found = static_cast<int>(q); break; }
       if (found < 0) atomicOr(A.err, ERRF_REVERSE);
       A.prev[p] = found < 0 ? static_cast<int>(p) : found;
     }
@@ -654,6 +652,15 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.err = m->err_flag.as<unsigned>();
   nb->masks.ensure(static_cast<size_t>(N) * kMaskWords * sizeof(uint32_t), s);
   A.mask = nb->masks.as<uint32_t>();
+  // the warp fill and the reverse record, when every configuration scans at most 32 bins
+  int max_scan = 0;
+  for (const DevCfg& C : cfgs) max_scan = std::max(max_scan, (2 * C.kb[0] + 1) * (2 * C.kb[1] + 1) * (2 * C.kb[2] + 1));
+  const bool warp_fill = max_scan <= kWarpScan;
+  A.rv = nullptr;
+  if (warp_fill) {
+    nb->segs.ensure(static_cast<size_t>(max_scan) * N * sizeof(uint2), s);
+    A.rv = nb->segs.as<uint2>();
+  }
   const int TB = 256;
   {
     ProfRegion pr1("neighbors_bin_count", s);
@@ -698,24 +705,12 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
   A.pimg = nb->pimg.as<int>();
   A.pr32 = nb->pr32.as<float4>();
   A.prev = nb->prev.as<int>();
-  A.seg = nullptr;
-  {
-    int max_scan = 0;
-    for (const DevCfg& C : cfgs) max_scan = std::max(max_scan, (2 * C.kb[0] + 1) * (2 * C.kb[1] + 1) * (2 * C.kb[2] + 1));
-    // the hints are 16-bit offsets into an atom's list; the search clamps them to the list, so a
-    // list longer than 65535 pairs only loses the hint (the whole list is searched)
-    if (max_scan < kSegStride) {
-      nb->segs.ensure(static_cast<size_t>(std::max<int64_t>(N, 1)) * kSegStride * sizeof(uint16_t) + P + 16, s);
-      A.seg = nb->segs.as<uint16_t>();
-      A.pq = reinterpret_cast<uint8_t*>(A.seg + static_cast<size_t>(std::max<int64_t>(N, 1)) * kSegStride);
-    }
-  }
-  // fill (at the counted offsets) and reverse pairs; a fill that disagrees with its count sets
-  // ERRF_CAPACITY: the pass is repeated once, then the build fails with MTP_ERR_CAPACITY
+  // fill (at the counted offsets) with the reverse pairs; a fill that disagrees with its count
+  // sets ERRF_CAPACITY: the pass is repeated once, then the build fails with MTP_ERR_CAPACITY
   for (int attempt = 0;; ++attempt) {
     {
       ProfRegion pr2("neighbors_fill", s);
-      if (A.seg) {
+      if (warp_fill) {
         k_fill_warp<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
         ProfRegion::launched();
       } else {
@@ -724,9 +719,9 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
       }
       MTP_CUDA(cudaGetLastError());
     }
-    if (total > 0) {
+    if (!warp_fill && total > 0) {
       ProfRegion pr3("neighbors_reverse", s);
-      k_reverse<<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
+      k_reverse<false><<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
       ProfRegion::launched();
       MTP_CUDA(cudaGetLastError());
     }
@@ -734,11 +729,22 @@ void build_neighbors(mtp_model* m, const mtp_batch* b, mtp_nbr* nb, cudaStream_t
     MTP_CUDA(cudaStreamSynchronize(s));
     if (take_injected(g_inject_overflow)) flag |= ERRF_CAPACITY;
     if (flag & ERRF_GEOMETRY) throw Fail{MTP_ERR_GEOMETRY, "coincident atoms (|r_ij| < 1e-8 A)"};
-    if (flag & ERRF_REVERSE) throw Fail{MTP_ERR_NUMERIC, "inconsistent neighbor list (reverse-pair mismatch)"};
     if (!(flag & ERRF_CAPACITY)) break;
     if (attempt == 1) throw Fail{MTP_ERR_CAPACITY, "neighbor fill overflowed its counted capacity twice"};
     MTP_CUDA(cudaMemsetAsync(m->err_flag.p, 0, sizeof(unsigned), s));
   }
+  if ((flag & ERRF_REVPEND) && !(flag & ERRF_REVERSE)) {
+    // atoms past slot 31 of their bin: their pairs' reverses by search
+    {
+      ProfRegion pr3("neighbors_reverse", s);
+      k_reverse<true><<<blocks_for(N * 32, 256), 256, 0, s>>>(A);
+      ProfRegion::launched();
+      MTP_CUDA(cudaGetLastError());
+    }
+    MTP_CUDA(cudaMemcpyAsync(&flag, m->err_flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    MTP_CUDA(cudaStreamSynchronize(s));
+  }
+  if (flag & ERRF_REVERSE) throw Fail{MTP_ERR_NUMERIC, "inconsistent neighbor list (reverse-pair mismatch)"};
   DevNbr& D = nb->dn;
   D.n_atoms = N;
   D.n_pairs = total;

@@ -9,6 +9,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2304_13144_gb300 import synth
+from nbr_check import check_reverse
 
 pytestmark = pytest.mark.gpu
 
@@ -98,6 +99,7 @@ def test_neighbor_list_matches_oracle(api, case):
     got = {(i, int(ex["j"][p]), *ex["img"][p]) for i in range(n) for p in range(ex["off"][i], ex["off"][i + 1])}
     want = {(i, int(ref["j"][p]), *ref["img"][p]) for i in range(n) for p in range(ref["off"][i], ref["off"][i + 1])}
     assert got == want
+    check_reverse(api, nb, b)
 
 
 # ---------------------------------------------------------------------------------

@@ -13,6 +13,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2304_13144_gb300 import synth
+from nbr_check import check_reverse
 
 pytestmark = pytest.mark.gpu
 
@@ -146,6 +147,12 @@ def test_million_atom_grade_with_maxvol_active_set(api, big, maxvol_set):
             assert np.all(np.abs(gc[act] - 1.0) <= mixed_grade_bound(1.0, S_c[act]))
             assert np.all(mixed_grade_ok(gc, ref_c, S_c))
     api.mtp_set_active_set(model, torch.tensor(synth.diag_dominant(8, big["md"].m), device="cuda"))
+
+
+def test_million_atom_reverse_pairs(api, big):
+    """Every one of the 47 M pairs' reverse index (formed by the fill pass from the count pass's
+    per-bin record) names the pair (j -> i, -n)."""
+    check_reverse(api, big["nb"], big["b"])
 
 
 def test_million_atom_invariants(big):
