@@ -209,10 +209,14 @@ constexpr int kWarpScan = 32;    // the warp fill and the reverse record: at mos
 constexpr int kMaskWords = 16;   // accepted-candidate bits per atom recorded by the count pass
 constexpr int kMaskBits = 32 * kMaskWords;
 
-// (at most 48 registers, 10 CTAs of 128 threads per SM: measured faster than 66 registers and
-// 7 CTAs despite a few spilled loop variables)
+// (at most 64 registers, 8 CTAs of 128 threads per SM: with the per-bin reverse record the
+// count pass measured 1.77 ms at 1M atoms against 1.91 ms at 48 registers / 10 CTAs and at
+// 80 registers / 6 CTAs; a warp-per-atom count pass with ballots measured 2.86 ms)
+#ifndef MTP_NB_MINB
+#define MTP_NB_MINB 8
+#endif
 template <bool FILL>
-__global__ void __launch_bounds__(128, 10) k_pairs(NbrArgs A) {
+__global__ void __launch_bounds__(128, MTP_NB_MINB) k_pairs(NbrArgs A) {
   // threads take the atoms in bin order, so that a warp's atoms scan the same or adjacent bins
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= A.n_atoms) return;
