@@ -608,7 +608,9 @@ def run_ours(args):
         "roofline": roof,
         "roofline_kernels": {k: roof_of(k) for k in per_step if k in work and k != dominant and roof_of(k)},
         "mixed_pass": dict(zip(("setting", "in_use", "split_warps", "split_nb"), api.mtp_get_mixed_pass(model)),
-                           requested=args.mixed_pass),
+                           requested=args.mixed_pass,
+                           **dict(zip(("split_unroll", "split_schedule", "split_schedule_global"),
+                                      api.mtp_get_split_shape(model)[2:]))),
         "measured_peaks": measured, "kernels": kernels, "gpu_launches": launches, "clocks": clk,
         "e2e": e2e,
     }
@@ -806,7 +808,8 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-peaks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (fixed launch sequence)")
-    ap.add_argument("--split-shape", default="", help="warps_pair,nb_contract of the three-kernel pass (no autotune)")
+    ap.add_argument("--split-shape", default="",
+                    help="warps_pair,nb_contract[,unroll[,schedule]] of the three-kernel pass (no autotune)")
     ap.add_argument("--cells", type=int, default=0, help="C4 only: n^3 fcc cells instead of 64^3 (profiling)")
     ap.add_argument("--mixed-pass", default="auto", choices=["auto", "single", "split"],
                     help="mixed path: the autotuner's choice, the single kernel or the three kernels")

@@ -72,7 +72,8 @@ _SIGS = {
     "mtp_sync": (ctypes.c_int, [_P, _P]),
     "mtp_set_mixed_pass": (ctypes.c_int, [_P, ctypes.c_int]),
     "mtp_get_mixed_pass": (ctypes.c_int, [_P, _P, _P, _P, _P]),
-    "mtp_set_split_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mtp_set_split_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mtp_get_split_shape": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "mtp_measure_peak": (ctypes.c_int, [ctypes.c_int, _P, _P, _P]),
     "mtp_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
     "mtp_fit_bfgs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _I64, _D, _P, _P, _P]),
@@ -525,8 +526,16 @@ def mtp_set_mixed_pass(model, p):
     _check(lib().mtp_set_mixed_pass(model.h, int(p)))
 
 
-def mtp_set_split_shape(model, warps_pair=0, nb_contract=0, unroll=0):
-    _check(lib().mtp_set_split_shape(model.h, int(warps_pair), int(nb_contract), int(unroll)))
+def mtp_set_split_shape(model, warps_pair=0, nb_contract=0, unroll=0, schedule=0):
+    """schedule: 0 automatic, 1 shared memory, 2 global memory (the contraction's schedule)."""
+    _check(lib().mtp_set_split_shape(model.h, int(warps_pair), int(nb_contract), int(unroll), int(schedule)))
+
+
+def mtp_get_split_shape(model):
+    """(warps_pair, nb_contract, unroll, schedule setting, last pass read the schedule from global memory)."""
+    v = [ctypes.c_int32() for _ in range(5)]
+    _check(lib().mtp_get_split_shape(model.h, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def mtp_get_mixed_pass(model):

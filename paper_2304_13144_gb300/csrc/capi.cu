@@ -793,6 +793,11 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     }
     int& knob = fast ? md->tune_warps_fast : md->tune_warps_generic;
     const int max_w = fast ? 8 : 4;
+    // the three-kernel pass replaces the generic kernel in mixed precision where the shape has
+    // one: the generic kernel is then timed at its default shape only (seconds per pass at
+    // level 24)
+    const bool split_ok = md->split_tab.p && prec == MTP_MIXED && md->mixed_pass != 1;
+    const int min_w = (!fast && split_ok) ? max_w : 1;
     cudaEvent_t e0, e1;
     MTP_CUDA(cudaEventCreate(&e0));
     MTP_CUDA(cudaEventCreate(&e1));
@@ -805,7 +810,7 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     for (int place = 0; place < (fast ? 2 : 1); ++place) {
       if (fast) md->tune_fwd_global = place;
       int last_used = -1;
-      for (int w = max_w; w >= 1; --w) {
+      for (int w = max_w; w >= min_w; --w) {
         knob = w;
         run();   // warm-up at this shape
         if (fast && static_cast<int>(md->last_fwd_global) != place) break;   // placement unavailable
@@ -825,21 +830,24 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
       }
     }
     // the three-kernel mixed pass, when the model has one: warps per block of its per-pair
-    // kernels x neighborhoods per warp of its contraction (results are the same for every shape)
-    int best_sw = 0, best_snb = 0, best_sun = 0;
+    // kernels x neighborhoods per warp of its contraction x words in flight x schedule placement
+    // (results are the same for every shape)
+    int best_sw = 0, best_snb = 0, best_sun = 0, best_sg = 0;
     float best_split = 0.f;
     const int keep_split = md->tune_split;
     md->mixed_pass = keep_pass;
-    if (fast && md->split_tab.p && keep_pass != 1) {
+    if (split_ok) {
       md->tune_split = 1;
+      for (int sg : {1, 2})
       for (int sw : {4, 8})
         for (int sc : {12, 14, 22, 24}) {
           const int snb = sc / 10, sun = sc % 10;
           md->tune_split_warps = sw;
           md->tune_split_nb = snb;
           md->tune_split_unroll = sun;
+          md->tune_split_gsch = sg;
           run();
-          if (!md->last_split) continue;
+          if (!md->last_split || static_cast<int>(md->last_split_gsch) + 1 != sg) continue;   // placement unavailable
           float t_min = 0.f;
           for (int rep = 0; rep < 3; ++rep) {
             MTP_CUDA(cudaEventRecord(e0, s));
@@ -850,7 +858,9 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
             MTP_CUDA(cudaEventElapsedTime(&t, e0, e1));
             if (rep == 0 || t < t_min) t_min = t;
           }
-          if (best_sw == 0 || t_min < best_split) { best_split = t_min; best_sw = sw; best_snb = snb; best_sun = sun; }
+          if (best_sw == 0 || t_min < best_split) {
+            best_split = t_min; best_sw = sw; best_snb = snb; best_sun = sun; best_sg = sg;
+          }
         }
       md->tune_split = keep_split;
     }
@@ -862,6 +872,7 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
       md->tune_split_warps = best_sw;
       md->tune_split_nb = best_snb;
       md->tune_split_unroll = best_sun;
+      md->tune_split_gsch = best_sg;
       const bool split = md->mixed_pass == 2 || best_split < best_ms;
       if (md->mixed_pass == 0) md->tune_split = split ? 1 : 0;
       if (split) best_ms = best_split;
@@ -891,15 +902,29 @@ mtp_status mtp_set_mixed_pass(mtp_model* md, int pass) {
   });
 }
 
-mtp_status mtp_set_split_shape(mtp_model* md, int warps_pair, int nb_contract, int unroll) {
+mtp_status mtp_set_split_shape(mtp_model* md, int warps_pair, int nb_contract, int unroll, int schedule) {
   return guarded([&] {
     check_model(md);
     if (warps_pair != 0 && warps_pair != 4 && warps_pair != 8) throw Fail{MTP_ERR_ARG, "warps_pair must be 0, 4 or 8"};
     if (nb_contract < 0 || nb_contract > 2) throw Fail{MTP_ERR_ARG, "nb_contract must be 0, 1 or 2"};
     if (unroll != 0 && unroll != 2 && unroll != 4) throw Fail{MTP_ERR_ARG, "unroll must be 0, 2 or 4"};
+    if (schedule < 0 || schedule > 2) throw Fail{MTP_ERR_ARG, "schedule must be 0, 1 or 2"};
     md->tune_split_warps = warps_pair;
     md->tune_split_nb = nb_contract;
     md->tune_split_unroll = unroll;
+    md->tune_split_gsch = schedule;
+  });
+}
+
+mtp_status mtp_get_split_shape(const mtp_model* md, int32_t* warps_pair, int32_t* nb_contract, int32_t* unroll,
+                               int32_t* schedule, int32_t* schedule_global) {
+  return guarded([&] {
+    if (!md) throw Fail{MTP_ERR_ARG, "null model"};
+    if (warps_pair) *warps_pair = md->tune_split_warps;
+    if (nb_contract) *nb_contract = md->tune_split_nb;
+    if (unroll) *unroll = md->tune_split_unroll;
+    if (schedule) *schedule = md->tune_split_gsch;
+    if (schedule_global) *schedule_global = md->last_split_gsch ? 1 : 0;
   });
 }
 

@@ -87,12 +87,15 @@ struct Tab {
   static constexpr SlotTab<Shape<NR, NU0>::NCOMP> slots = make_slots<NR, NU0>();
 };
 
+// f(integral_constant<I>), f(integral_constant<I + 1>), ..., f(integral_constant<N - 1>) in order
+// (a fold over an index sequence: no recursion depth, for the 286 monomials of degree <= 10)
+template <int I, class F, int... K>
+__device__ __forceinline__ void static_for_seq(F& f, std::integer_sequence<int, K...>) {
+  (f(std::integral_constant<int, I + K>{}), ...);
+}
 template <int I, int N, class F>
 __device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (I < N) {
-    f(std::integral_constant<int, I>{});
-    static_for<I + 1, N>(f);
-  }
+  if constexpr (I < N) static_for_seq<I>(f, std::make_integer_sequence<int, N - I>{});
 }
 
 __device__ __forceinline__ float axis_val(int ax, float x, float y, float z) { return ax == 0 ? x : (ax == 1 ? y : z); }

@@ -42,6 +42,13 @@ constexpr int BATCH = 64;    // pairs staged per neighborhood at a time (moments
 constexpr int BATCH_A = 32;  // pairs staged per neighborhood at a time (pair adjoint)
 constexpr int GS = 17;       // floats staged per pair for the radial block: g_mu, Q_b, species (odd)
 
+// float4 arrays staged per pair by the moment kernel: (x, y, z, f_0), then f_1.. four at a time
+__host__ __device__ constexpr int stage_f4(int nr) { return 1 + (nr - 1 + 3) / 4; }
+// moment components held per lane by the contraction kernel (n_mom <= 32 PRE) and the species
+// of the radial-block accumulators of the pair-adjoint kernel, per shape
+__host__ __device__ constexpr int pre_of(int nr) { return nr <= 5 ? 10 : 19; }
+__host__ __device__ constexpr int tmax_of(int nr) { return nr <= 5 ? 3 : 4; }
+
 // shared-memory floats per neighborhood group of the pair-adjoint kernel: dV/dM (ldm rounded up
 // to 32, plus 8) then the radial-block staging; the stride is 8 mod 32 banks, so the four groups'
 // broadcast reads of one component hit four different banks, and with the odd per-pair stride
@@ -164,7 +171,7 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
   using Tb = Tab<NR, NU0>;
   using CI = ChunkInfo<NR, NU0>;
   constexpr int NQ = kNQs;
-  static_assert(NR <= 5, "the staging holds f_0 .. f_4");
+  constexpr int NF4 = stage_f4(NR);
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
   float* ctab = reinterpret_cast<float*>(smem);
@@ -173,10 +180,10 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
     if (OK(T + d.n_lin + k, d.n_params, 1)) ctab[k] = d.theta_f[T + d.n_lin + k];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / LPN, q = lane % LPN;
   const int nwarps = blockDim.x >> 5;
-  // per group: (x, y, z, f_0) and (f_1 .. f_4) of each staged pair as two float4 arrays; the 8
-  // lanes of a group read 8 consecutive float4 (one conflict-free phase of a 128-bit load)
-  float4* stgA = reinterpret_cast<float4*>(smem + P.c_bytes) + (static_cast<size_t>(warp) * GPW + grp) * 2 * BATCH;
-  float4* stgB = stgA + BATCH;
+  // per group: (x, y, z, f_0), (f_1 .. f_4), (f_5, 0, 0, 0) of each staged pair as NF4 float4
+  // arrays; the 8 lanes of a group read 8 consecutive float4 (one conflict-free phase of a
+  // 128-bit load)
+  float4* stg = reinterpret_cast<float4*>(smem + P.c_bytes) + (static_cast<size_t>(warp) * GPW + grp) * NF4 * BATCH;
   __syncthreads();
   const float rmin = static_cast<float>(d.r_min), rcut = static_cast<float>(d.r_cut);
   for (int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * GPW; w0 < P.n_work;
@@ -211,11 +218,12 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
         if (!OK(zj, T, 9)) continue;
         float f[NR], df[NR];
         radial<NR, NQ>(r.w, czi + zj * NR * NQ, rmin, rcut, f, df, nullptr);
-        float fe[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float fe[4 * NF4 - 3];
 #pragma unroll
-        for (int mu = 0; mu < NR; ++mu) fe[mu] = f[mu];
-        stgA[t] = make_float4(r.x, r.y, r.z, fe[0]);
-        stgB[t] = make_float4(fe[1], fe[2], fe[3], fe[4]);
+        for (int k = 0; k < 4 * NF4 - 3; ++k) fe[k] = k < NR ? f[k < NR ? k : 0] : 0.f;
+        stg[t] = make_float4(r.x, r.y, r.z, fe[0]);
+#pragma unroll
+        for (int k = 1; k < NF4; ++k) stg[k * BATCH + t] = make_float4(fe[4 * k - 3], fe[4 * k - 2], fe[4 * k - 1], fe[4 * k]);
       }
       __syncwarp();
       static_for<0, Sh::NCHUNK>([&](auto Cc) {
@@ -226,12 +234,18 @@ __global__ void __launch_bounds__(256) k_moments(SplitArgs P) {
         for (int t = 0; t < 32; ++t) acc[t] = 0.f;
         for (int t = q; t < nbt; t += LPN) {
           if (!OK(t, BATCH, 10)) continue;
-          const float4 ea = stgA[t], eb = stgB[t];
+          const float4 ea = stg[t];
           const float x = ea.x, y = ea.y, z = ea.z;
-          const float fe[5] = {ea.w, eb.x, eb.y, eb.z, eb.w};
           float f[NR];
+          f[0] = ea.w;
 #pragma unroll
-          for (int mu = 0; mu < NR; ++mu) f[mu] = fe[mu];
+          for (int k = 1; k < NF4; ++k) {
+            const float4 eb = stg[k * BATCH + t];
+            const float e4[4] = {eb.x, eb.y, eb.z, eb.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (4 * k - 3 + u < NR) f[4 * k - 3 + u < NR ? 4 * k - 3 + u : 0] = e4[u];
+          }
           float px[DH + 1], py[DH + 1], pz[DH + 1];
           px[0] = py[0] = pz[0] = 1.f;
 #pragma unroll
@@ -276,8 +290,6 @@ __device__ __forceinline__ void copy_words_s(uint32_t* dst, const uint32_t* src,
   for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
-constexpr int kMaxPre = 10;   // moment components per lane held in registers (n_mom <= 320)
-
 // one slab word: a += c v[x] v[y] (forward) or a += c v[x] g[y] (reverse, w = the adjoint array)
 template <int NB, bool INL>
 __device__ __forceinline__ void slab_term(uint32_t wd, const float* coef, float* const (&v)[NB], float* const (&w)[NB],
@@ -297,9 +309,13 @@ __device__ __forceinline__ void slab_term(uint32_t wd, const float* coef, float*
   for (int j = 0; j < NB; ++j) a[j] = fmaf(c, v[j][x] * w[j][y], a[j]);
 }
 
-// one round of 32 destination lists (L words per lane, lane stride 32): UNR words in flight,
-// word it always added to chain it % 2 (the sum is the same for every UNR, bit for bit)
-template <int NB, bool INL, int UNR>
+// one round of 32 destination lists (L words per lane, lane stride 32), UNR words per step;
+// word it always goes to chain it % 2 (the sum is the same for every UNR and both loops, bit
+// for bit).  Schedule in shared memory: the next step's words are loaded while the current ones
+// are used (1.03x at level 20).  Schedule in global memory (GSCH): words read through the
+// read-only path, one step at a time (loading a step ahead measured 1.5x slower at level 24;
+// an L1 prefetch 8-64 rows ahead and the barrier interval changed nothing).
+template <int NB, bool INL, int UNR, bool GSCH = false>
 __device__ __forceinline__ void slab_round(const uint32_t* slab, int L, const float* coef, float* const (&v)[NB],
                                            float* const (&w)[NB], float (&acc)[NB]) {
   static_assert(UNR % 2 == 0, "whole pairs of words per iteration");
@@ -308,15 +324,35 @@ __device__ __forceinline__ void slab_round(const uint32_t* slab, int L, const fl
   for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int j = 0; j < NB; ++j) a[u][j] = 0.f;
-  int it = 0;
-  for (; it + UNR <= L; it += UNR) {
-    uint32_t wd[UNR];
+  const int LU = L - L % UNR;   // rows of the whole steps
+  if constexpr (GSCH) {
+    for (int it = 0; it < LU; it += UNR) {
+      uint32_t wd[UNR];
 #pragma unroll
-    for (int u = 0; u < UNR; ++u) wd[u] = slab[32 * (it + u)];
+      for (int u = 0; u < UNR; ++u) wd[u] = __ldg(slab + 32 * (it + u));
 #pragma unroll
-    for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u & 1]);
+      for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u & 1]);
+    }
+    for (int it = LU; it < L; ++it) slab_term<NB, INL>(__ldg(slab + 32 * it), coef, v, w, a[it & 1]);
+  } else {
+    uint32_t nxt[UNR];
+    if (LU > 0) {
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) nxt[u] = slab[32 * u];
+    }
+    for (int it = 0; it < LU; it += UNR) {
+      uint32_t wd[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) wd[u] = nxt[u];
+      if (it + UNR < LU) {
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) nxt[u] = slab[32 * (it + UNR + u)];
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u & 1]);
+    }
+    for (int it = LU; it < L; ++it) slab_term<NB, INL>(slab[32 * it], coef, v, w, a[it & 1]);
   }
-  for (; it < L; ++it) slab_term<NB, INL>(slab[32 * it], coef, v, w, a[it & 1]);
 #pragma unroll
   for (int j = 0; j < NB; ++j) acc[j] += a[0][j] + a[1][j];
 }
@@ -336,7 +372,16 @@ __device__ __forceinline__ void group_combine(float (&acc)[NB], int ent) {
   }
 }
 
-template <int NB, bool INL, int UNR>
+// PRE: moment components per lane prefetched in registers (n_mom <= 32 PRE).  GSCH: the schedule
+// stays in global memory (a level whose schedule does not fit shared memory next to the value
+// arrays): the block's warps meet at a barrier every round, so that they walk the schedule
+// together and each round's words are fetched from L2 once per block and then hit in L1; every
+// warp of a block runs the same number of neighborhood iterations (a warp past the end computes
+// on zeros and writes nothing).
+#ifndef MTP_GSCH_SYNC
+#define MTP_GSCH_SYNC 1   // rounds between the block's barriers in the global-schedule variant
+#endif
+template <int NB, bool INL, int UNR, int PRE, bool GSCH>
 __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
@@ -344,25 +389,42 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   float* coef = reinterpret_cast<float*>(smem);
   for (int k = threadIdx.x; k < d.n_coef; k += blockDim.x)
     if (OK(k * 4 + 3, static_cast<long long>(P.c_bytes), 20)) coef[k] = d.coef_f[k];
-  uint32_t* sched = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
-  copy_words_s(sched + P.o_fslab, d.pfslab, d.pfslab_words);
-  copy_words_s(sched + P.o_fround, reinterpret_cast<const uint32_t*>(d.pfround), 4 * d.n_pfround);
-  copy_words_s(sched + P.o_frdst, reinterpret_cast<const uint32_t*>(d.pfr_dst), 32 * d.n_pfround);
-  copy_words_s(sched + P.o_rslab, d.prslab, d.prslab_words);
-  copy_words_s(sched + P.o_rround, reinterpret_cast<const uint32_t*>(d.prround), 4 * d.n_prround);
-  copy_words_s(sched + P.o_rrval, reinterpret_cast<const uint32_t*>(d.prr_val), 32 * d.n_prround);
-  copy_words_s(sched + P.o_seed, reinterpret_cast<const uint32_t*>(d.seed_f), d.n_vals);
-  const uint32_t* s_fslab = sched + P.o_fslab;
-  const int4* s_fround = reinterpret_cast<const int4*>(sched + P.o_fround);
-  const int* s_frdst = reinterpret_cast<const int*>(sched + P.o_frdst);
-  const uint32_t* s_rslab = sched + P.o_rslab;
-  const int4* s_rround = reinterpret_cast<const int4*>(sched + P.o_rround);
-  const int* s_rrval = reinterpret_cast<const int*>(sched + P.o_rrval);
-  const float* s_seed = reinterpret_cast<const float*>(sched + P.o_seed);
+  const uint32_t* s_fslab;
+  const int4* s_fround;
+  const int* s_frdst;
+  const uint32_t* s_rslab;
+  const int4* s_rround;
+  const int* s_rrval;
+  const float* s_seed;
+  if constexpr (GSCH) {
+    s_fslab = d.pfslab;
+    s_fround = reinterpret_cast<const int4*>(d.pfround);
+    s_frdst = d.pfr_dst;
+    s_rslab = d.prslab;
+    s_rround = reinterpret_cast<const int4*>(d.prround);
+    s_rrval = d.prr_val;
+    s_seed = d.seed_f;
+  } else {
+    uint32_t* sched = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
+    copy_words_s(sched + P.o_fslab, d.pfslab, d.pfslab_words);
+    copy_words_s(sched + P.o_fround, reinterpret_cast<const uint32_t*>(d.pfround), 4 * d.n_pfround);
+    copy_words_s(sched + P.o_frdst, reinterpret_cast<const uint32_t*>(d.pfr_dst), 32 * d.n_pfround);
+    copy_words_s(sched + P.o_rslab, d.prslab, d.prslab_words);
+    copy_words_s(sched + P.o_rround, reinterpret_cast<const uint32_t*>(d.prround), 4 * d.n_prround);
+    copy_words_s(sched + P.o_rrval, reinterpret_cast<const uint32_t*>(d.prr_val), 32 * d.n_prround);
+    copy_words_s(sched + P.o_seed, reinterpret_cast<const uint32_t*>(d.seed_f), d.n_vals);
+    s_fslab = sched + P.o_fslab;
+    s_fround = reinterpret_cast<const int4*>(sched + P.o_fround);
+    s_frdst = reinterpret_cast<const int*>(sched + P.o_frdst);
+    s_rslab = sched + P.o_rslab;
+    s_rround = reinterpret_cast<const int4*>(sched + P.o_rround);
+    s_rrval = reinterpret_cast<const int*>(sched + P.o_rrval);
+    s_seed = reinterpret_cast<const float*>(sched + P.o_seed);
+  }
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // per warp: NB (values, adjoints) array pairs, each adjoint array NV after its values
-  float* const wbase = reinterpret_cast<float*>(smem + P.c_bytes + P.sched_bytes + warp * P.warp_bytes);
+  float* const wbase = reinterpret_cast<float*>(smem + P.c_bytes + (GSCH ? 0 : P.sched_bytes) + warp * P.warp_bytes);
   for (int k = lane; k < 2 * NB * NV; k += 32) wbase[k] = 0.f;   // the zero slot n_vals stays 0
   float* v[NB];
   float* g[NB];
@@ -374,9 +436,9 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   const int T = P.T;
   const int n_mom = d.n_mom;
   // this lane's moment slots (the same for every neighborhood) and their value indices
-  int sc[kMaxPre];
+  int sc[PRE];
 #pragma unroll
-  for (int r = 0; r < kMaxPre; ++r) {
+  for (int r = 0; r < PRE; ++r) {
     const int k = lane + 32 * r;
     sc[r] = k < n_mom ? P.slot_comp[k] : -1;
     if (sc[r] >= 0 && !OK(sc[r], NV, 21)) sc[r] = -1;
@@ -384,23 +446,25 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * nwarps * NB;
   // moments of the next neighborhoods, loaded one iteration ahead (their global latency overlaps
   // the contraction of the current ones)
-  float pre[NB][kMaxPre];
+  float pre[NB][PRE];
   auto fetch = [&](int64_t w0) {
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       const bool live = w0 + j < P.n_work;
       const float* src = P.mom + (w0 + j) * P.ldm;
 #pragma unroll
-      for (int r = 0; r < kMaxPre; ++r) {
+      for (int r = 0; r < PRE; ++r) {
         const int k = lane + 32 * r;
         pre[j][r] = (live && sc[r] >= 0 && OK((w0 + j) * P.ldm + k, P.n_work * P.ldm, 22)) ? __ldcs(src + k) : 0.f;
       }
     }
   };
-  int64_t w0 = (static_cast<int64_t>(blockIdx.x) * nwarps + warp) * NB;
+  // the block's first neighborhood: with GSCH the loop runs while the block has any work left
+  const int64_t bfirst = static_cast<int64_t>(blockIdx.x) * nwarps * NB;
+  int64_t w0 = bfirst + static_cast<int64_t>(warp) * NB;
   if (w0 < P.n_work) fetch(w0);
   __syncthreads();
-  for (; w0 < P.n_work; w0 += stride) {
+  for (int64_t b0 = bfirst; GSCH ? b0 < P.n_work : w0 < P.n_work; b0 += stride, w0 += stride) {
     int64_t wk[NB];
     bool live[NB];
 #pragma unroll
@@ -408,8 +472,8 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
       wk[j] = w0 + j;
       live[j] = wk[j] < P.n_work;
 #pragma unroll
-      for (int r = 0; r < kMaxPre; ++r)
-        if (sc[r] >= 0) v[j][sc[r]] = pre[j][r];
+      for (int r = 0; r < PRE; ++r)
+        if (sc[r] >= 0) v[j][sc[r]] = live[j] ? pre[j][r] : 0.f;
     }
     if (w0 + stride < P.n_work) fetch(w0 + stride);
     __syncwarp();
@@ -417,6 +481,9 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
     int4 rd_n = d.n_pfround > 0 ? s_fround[0] : make_int4(0, 0, 0, 0);
     int dst_n = d.n_pfround > 0 ? s_frdst[lane] : -1;
     for (int r = 0; r < d.n_pfround; ++r) {
+      if constexpr (GSCH && MTP_GSCH_SYNC > 0) {
+        if (r % MTP_GSCH_SYNC == 0) __syncthreads();
+      }
       int4 rd = rd_n;
       const int ent = dst_n;
       if (r + 1 < d.n_pfround) {
@@ -427,7 +494,7 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
       float acc[NB];
 #pragma unroll
       for (int j = 0; j < NB; ++j) acc[j] = 0.f;
-      slab_round<NB, INL, UNR>(s_fslab + rd.y + lane, rd.x, coef, v, v, acc);
+      slab_round<NB, INL, UNR, GSCH>(s_fslab + rd.y + lane, rd.x, coef, v, v, acc);
       if (rd.w) group_combine<NB>(acc, ent);
       const int dst = ent & 0xffff;
       if (ent >= 0 && ((ent >> 20) & 1) && OK(dst, NV, 26)) {
@@ -454,6 +521,9 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
     int x_n = d.n_prround > 0 ? s_rrval[lane] : -1;
     int x_nn = d.n_prround > 1 ? s_rrval[32 + lane] : -1;
     for (int r = 0; r < d.n_prround; ++r) {
+      if constexpr (GSCH && MTP_GSCH_SYNC > 0) {
+        if (r % MTP_GSCH_SYNC == 0) __syncthreads();
+      }
       int4 rd = rd_n;
       const int ent = x_n;
       if (r + 1 < d.n_prround) {
@@ -468,7 +538,7 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
       float acc[NB];
 #pragma unroll
       for (int j = 0; j < NB; ++j) acc[j] = sd;
-      slab_round<NB, INL, UNR>(s_rslab + rd.y + lane, rd.x, coef, v, g, acc);
+      slab_round<NB, INL, UNR, GSCH>(s_rslab + rd.y + lane, rd.x, coef, v, g, acc);
       if (rd.w) group_combine<NB>(acc, ent);
       if (lead && OK(x, NV, 32)) {
 #pragma unroll
@@ -483,7 +553,7 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
       if (!live[j]) continue;
       float* dst = P.mom + wk[j] * P.ldm;
 #pragma unroll
-      for (int r = 0; r < kMaxPre; ++r)
+      for (int r = 0; r < PRE; ++r)
         if (sc[r] >= 0 && OK(wk[j] * P.ldm + lane + 32 * r, P.n_work * P.ldm, 34)) __stcs(dst + lane + 32 * r, g[j][sc[r]]);
       const int64_t i = atom_of(P, wk[j]);
       const int64_t rw = P.o.row_pos ? P.o.row_pos[i] : wk[j];
@@ -556,9 +626,10 @@ __global__ void __launch_bounds__(256) k_adjoint(SplitArgs P) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) Wl[k] = 0.f;
     // radial block accumulators: lane q owns beta = q for every (species, mu)
-    float cb[3][NR];
+    constexpr int TM = tmax_of(NR);
+    float cb[TM][NR];
 #pragma unroll
-    for (int z = 0; z < 3; ++z)
+    for (int z = 0; z < TM; ++z)
 #pragma unroll
       for (int mu = 0; mu < NR; ++mu) cb[z][mu] = 0.f;
     float* Gout = static_cast<float*>(P.o.G);
@@ -623,7 +694,7 @@ __global__ void __launch_bounds__(256) k_adjoint(SplitArgs P) {
           for (int mu = 0; mu < NR; ++mu) {
             const float pr = e[mu] * qb;
 #pragma unroll
-            for (int z = 0; z < 3; ++z) cb[z][mu] += (zj == z) ? pr : 0.f;
+            for (int z = 0; z < TM; ++z) cb[z][mu] += (zj == z) ? pr : 0.f;
           }
         }
         __syncwarp();
@@ -658,7 +729,7 @@ __global__ void __launch_bounds__(256) k_adjoint(SplitArgs P) {
         if (e / P.CBN != zi || k >= d.n_params) put(k, 0.f);
       }
 #pragma unroll
-      for (int z = 0; z < 3; ++z) {
+      for (int z = 0; z < TM; ++z) {
         if (z < T) {
 #pragma unroll
           for (int mu = 0; mu < NR; ++mu) put(off_c + static_cast<int64_t>(zi) * P.CBN + (z * NR + mu) * NQ + q, cb[z][mu]);
@@ -684,13 +755,13 @@ int num_sms() {
 }
 
 template <int NR, int NU0>
-void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool efs, bool rows, cudaStream_t s) {
-  constexpr int NQ = kNQs;
+void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool gsch, bool efs, bool rows,
+                  cudaStream_t s) {
   const int nsm = num_sms();
   const int64_t groups = (P.n_work + GPW - 1) / GPW;
   // ---- moments ----
   {
-    const size_t smem = P.c_bytes + static_cast<size_t>(warps_pair) * GPW * 2 * BATCH * sizeof(float4);
+    const size_t smem = P.c_bytes + static_cast<size_t>(warps_pair) * GPW * stage_f4(NR) * BATCH * sizeof(float4);
     auto kern = k_moments<NR, NU0>;
     MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     const int per = blocks_per_sm(kern, warps_pair * 32, smem);
@@ -703,12 +774,12 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool
   }
   // ---- contraction ----
   {
-    const size_t smem = P.total;
-    const int wpb = std::max(1, static_cast<int>((227 * 1024 - P.c_bytes - P.sched_bytes) / P.warp_bytes));
+    const size_t sched = gsch ? 0 : P.sched_bytes;
+    const int wpb = std::max(1, static_cast<int>((227 * 1024 - P.c_bytes - sched) / P.warp_bytes));
     const int warps = std::min(wpb, 16);
     const bool inl = P.d.coef_inline;
     auto launch = [&](auto kern) {
-      const size_t sm = P.c_bytes + P.sched_bytes + static_cast<size_t>(warps) * P.warp_bytes;
+      const size_t sm = P.c_bytes + sched + static_cast<size_t>(warps) * P.warp_bytes;
       MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
       const int per = blocks_per_sm(kern, warps * 32, sm);
       const int64_t need = (P.n_work + nb_contract - 1) / nb_contract;
@@ -719,11 +790,20 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool
       ProfRegion::launched();
       MTP_CUDA(cudaGetLastError());
     };
-    (void)smem;
+    constexpr int PRE = pre_of(NR);
+    // the level-24 shape (6, 10) only has the global-schedule, 12-bit-index variant (its 3,853
+    // values need 12-bit indices, its schedule does not fit shared memory; the caller checks)
     auto pick = [&](auto nbc, auto unr) {
       constexpr int NBc = decltype(nbc)::value, U = decltype(unr)::value;
-      if (inl) launch(k_contract<NBc, true, U>);
-      else launch(k_contract<NBc, false, U>);
+      if constexpr (NR >= 6) {
+        launch(k_contract<NBc, false, U, PRE, true>);
+      } else if (gsch) {
+        if (inl) launch(k_contract<NBc, true, U, PRE, true>);
+        else launch(k_contract<NBc, false, U, PRE, true>);
+      } else {
+        if (inl) launch(k_contract<NBc, true, U, PRE, false>);
+        else launch(k_contract<NBc, false, U, PRE, false>);
+      }
     };
     if (nb_contract == 2) {
       if (unroll == 4) pick(std::integral_constant<int, 2>{}, std::integral_constant<int, 4>{});
@@ -771,6 +851,7 @@ void split_prepare(mtp_model* m) {
     else if (d.n_rad == 3 && d.nu_max == 4) t = slot_table<3, 4>();
     else if (d.n_rad == 4 && d.nu_max == 6) t = slot_table<4, 6>();
     else if (d.n_rad == 5 && d.nu_max == 8) t = slot_table<5, 8>();
+    else if (d.n_rad == 6 && d.nu_max == 10) t = slot_table<6, 10>();
   }
   if (t.empty() || static_cast<int>(t.size()) != d.n_mom) return;
   m->split_tab.ensure(t.size() * sizeof(int), 0);
@@ -783,15 +864,16 @@ void split_prepare(mtp_model* m) {
 bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const SiteOutputs& o, cudaStream_t s) {
   const DevSchedule& d = m->ds;
   float* mom_ws = o.mom;
-  if (!mom_ws || !split_wanted(m) || !d.tri_pk || d.n_q != kNQs || d.n_types > 3) return false;
+  if (!mom_ws || !split_wanted(m) || !d.tri_pk || d.n_q != kNQs || d.n_types > tmax_of(d.n_rad)) return false;
   if (o.rows || o.atom_list) return false;
   const bool efs = o.V != nullptr;
   const bool rows = o.rows_hi != nullptr;
   if (!efs && !rows) return false;
   if (efs && (!o.G || !o.Wat)) return false;
   const int nr = d.n_rad, nu0 = d.nu_max;
-  const bool shape_ok = (nr == 2 && nu0 == 2) || (nr == 3 && nu0 == 4) || (nr == 4 && nu0 == 6) || (nr == 5 && nu0 == 8);
-  if (!shape_ok || d.n_mom > 32 * kMaxPre) return false;
+  const bool shape_ok = (nr == 2 && nu0 == 2) || (nr == 3 && nu0 == 4) || (nr == 4 && nu0 == 6) ||
+                        (nr == 5 && nu0 == 8) || (nr == 6 && nu0 == 10);
+  if (!shape_ok || d.n_mom > 32 * pre_of(nr)) return false;
   SplitArgs P{};
   P.d = d;
   P.nb = nb->dn;
@@ -818,18 +900,24 @@ bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const 
   P.sched_bytes = static_cast<size_t>(w) * 4;
   const int nbc = m->tune_split_nb > 0 ? m->tune_split_nb : 1;
   P.warp_bytes = static_cast<size_t>(2 * nbc * P.NV) * sizeof(float);
-  if (P.c_bytes + P.sched_bytes + P.warp_bytes > 227 * 1024) return false;
-  P.total = P.c_bytes + P.sched_bytes + P.warp_bytes;
+  // the schedule in shared memory when it fits beside at least four warps' value arrays (unless
+  // global memory is asked for), else read from global memory (level 24: 0.4 MB of slab words)
+  const bool gsch = P.c_bytes + P.sched_bytes + 4 * P.warp_bytes > 227 * 1024 || m->tune_split_gsch == 2;
+  if ((nr >= 6 && !gsch) || (nr >= 6 && d.coef_inline)) return false;
+  if (P.c_bytes + (gsch ? 0 : P.sched_bytes) + P.warp_bytes > 227 * 1024) return false;
+  P.total = P.c_bytes + (gsch ? 0 : P.sched_bytes) + P.warp_bytes;
   const int wp = m->tune_split_warps > 0 ? m->tune_split_warps : 8;
   m->last_fast = true;
   m->last_split = true;
+  m->last_split_gsch = gsch;
   m->last_warps = wp;
   if (P.n_work == 0) return true;
   const int unr = m->tune_split_unroll == 4 ? 4 : 2;
-  if (nr == 2) launch_split<2, 2>(P, wp, nbc, unr, efs, rows, s);
-  else if (nr == 3) launch_split<3, 4>(P, wp, nbc, unr, efs, rows, s);
-  else if (nr == 4) launch_split<4, 6>(P, wp, nbc, unr, efs, rows, s);
-  else launch_split<5, 8>(P, wp, nbc, unr, efs, rows, s);
+  if (nr == 2) launch_split<2, 2>(P, wp, nbc, unr, gsch, efs, rows, s);
+  else if (nr == 3) launch_split<3, 4>(P, wp, nbc, unr, gsch, efs, rows, s);
+  else if (nr == 4) launch_split<4, 6>(P, wp, nbc, unr, gsch, efs, rows, s);
+  else if (nr == 5) launch_split<5, 8>(P, wp, nbc, unr, gsch, efs, rows, s);
+  else launch_split<6, 10>(P, wp, nbc, unr, gsch, efs, rows, s);
 #ifdef MTP_SPLIT_CHECK
   unsigned long long fault = 0;
   MTP_CUDA(cudaStreamSynchronize(s));

@@ -4,9 +4,11 @@ liquid-like random-sequential-addition configuration (0.085 atoms/A^3, minimum s
 
 * 300-atom periodic cube: every site energy, force, the virial and the parameter rows of a few
   atoms, FP64 and mixed paths.
+* the same cube through the three-kernel mixed pass (moments, contraction with the schedule
+  read from global memory, pair adjoint): every site energy, force, per-atom virial and grade.
 * 2,097,152 atoms (a 32,768-atom cube repeated 4 x 4 x 4, species drawn per atom), the step
-  with the grade: site energies, forces and grades of sampled atoms, plus zero net force and
-  a symmetric virial.
+  with the grade, through the FP64 path and both mixed passes: site energies, forces and
+  grades of sampled atoms, plus zero net force and a symmetric virial.
 """
 import numpy as np
 import pytest
@@ -65,6 +67,35 @@ def test_liquid_300_atoms_every_atom(api, model_l24, prec):
     assert np.abs(rows - ref_rows).max() <= tol * np.abs(ref_rows).max()
 
 
+def test_liquid_300_atoms_split_pass(api, model_l24):
+    md, theta = model_l24
+    bnp = synth.liquid_rsa(seed=5, n_atoms=300)
+    nbr = O.batch_neighbors(bnp, R_CUT)
+    ref = O.efs(md, theta, bnp, nbr)
+    rows = O.site_rows(md, theta, bnp["type"], nbr)
+    A = synth.diag_dominant(56, md.m)
+    gamma, _ = O.grade(A, rows)
+    model = api.mtp_load(api.make_desc(4, 24, r_cut=R_CUT), theta)
+    api.mtp_set_active_set(model, torch.tensor(A, device="cuda"))
+    b = api.Batch(bnp)
+    nb = api.mtp_build_neighbors(model, b)
+    n = len(bnp["type"])
+    outs = {}
+    for p in ("single", "split"):
+        api.mtp_set_mixed_pass(model, p)
+        assert api.mtp_get_mixed_pass(model)[1] == (2 if p == "split" else 1)
+        o = api.mtp_step(model, b, nb, "mixed", threshold=2.0)
+        o.update(api.mtp_energy_forces_stress_atoms(model, b, nb, "mixed"))
+        out = outs[p] = {k: v.cpu().numpy() for k, v in o.items() if v is not None}
+        assert np.abs(out["energy"] - ref["E"]).max() / n <= 1e-6
+        assert np.abs(out["site_energy"] - ref["V"]).max() <= 1e-6
+        assert np.abs(out["forces"] - ref["F"]).max() <= 1e-5
+        assert np.abs(out["virial"] - ref["W"]).max() <= 1e-5 * np.abs(ref["W"]).max()
+        assert np.all(np.abs(out["gamma"] - gamma) <= 1e-4 * np.maximum(1.0, gamma))
+    a, s2 = outs["single"], outs["split"]
+    assert np.abs(a["site_virial"] - s2["site_virial"]).max() <= 1e-5 * np.abs(a["site_virial"]).max()
+
+
 @pytest.fixture(scope="module")
 def big_liquid(api, model_l24):
     md, theta = model_l24
@@ -75,9 +106,11 @@ def big_liquid(api, model_l24):
     b = api.Batch(bnp)
     nb = api.mtp_build_neighbors(model, b)
     outs = {}
-    for prec in ("mixed", "fp64"):
-        o = api.mtp_step(model, b, nb, prec, threshold=2.0)
-        o["site_energy"] = api.mtp_energy_forces_stress(model, b, nb, prec)["site_energy"]
+    for prec, pas in (("mixed", "single"), ("mixed_split", "split"), ("fp64", "auto")):
+        api.mtp_set_mixed_pass(model, pas)
+        p = "fp64" if prec == "fp64" else "mixed"
+        o = api.mtp_step(model, b, nb, p, threshold=2.0)
+        o["site_energy"] = api.mtp_energy_forces_stress(model, b, nb, p)["site_energy"]
         outs[prec] = {k: (v.cpu().numpy() if v is not None else None) for k, v in o.items()}
         del o
         torch.cuda.empty_cache()
@@ -107,20 +140,26 @@ def big_liquid(api, model_l24):
 def test_liquid_2m_atoms_sampled(big_liquid):
     big = big_liquid
     k = big["sample"]
-    o64, omx = big["outs"]["fp64"], big["outs"]["mixed"]
+    o64 = big["outs"]["fp64"]
     np.testing.assert_allclose(o64["site_energy"][k], big["V"], rtol=1e-10, atol=1e-10 * np.abs(big["V"]).max())
-    assert np.abs(omx["site_energy"][k] - big["V"]).max() <= 1e-6
     scale = max(1.0, np.abs(big["F"]).max())
     assert np.abs(o64["forces"][k] - big["F"]).max() <= 1e-10 * scale
-    assert np.abs(omx["forces"][k] - big["F"]).max() <= 1e-5
     np.testing.assert_allclose(o64["gamma"][k], big["gamma"], rtol=1e-10)
     assert (o64["argmax"][k] == big["argmax"]).all()
     g = big["gamma"]
-    assert np.all(np.abs(omx["gamma"][k] - g) <= 1e-4 * np.maximum(1.0, g))
+    for name in ("mixed", "mixed_split"):
+        omx = big["outs"][name]
+        assert np.abs(omx["site_energy"][k] - big["V"]).max() <= 1e-6, name
+        assert np.abs(omx["forces"][k] - big["F"]).max() <= 1e-5, name
+        assert np.all(np.abs(omx["gamma"][k] - g) <= 1e-4 * np.maximum(1.0, g)), name
+    # the two mixed passes on every atom
+    a, s2 = big["outs"]["mixed"], big["outs"]["mixed_split"]
+    assert np.abs(a["forces"] - s2["forces"]).max() <= 2e-5
+    assert np.abs(a["site_energy"] - s2["site_energy"]).max() <= 2e-6
 
 
 def test_liquid_2m_atoms_invariants(big_liquid):
-    for prec, tol in (("fp64", 1e-9), ("mixed", 1e-3)):
+    for prec, tol in (("fp64", 1e-9), ("mixed", 1e-3), ("mixed_split", 1e-3)):
         o = big_liquid["outs"][prec]
         F = o["forces"]
         assert np.isfinite(F).all()
