@@ -309,13 +309,11 @@ __device__ __forceinline__ void slab_term(uint32_t wd, const float* coef, float*
   for (int j = 0; j < NB; ++j) a[j] = fmaf(c, v[j][x] * w[j][y], a[j]);
 }
 
-// one round of 32 destination lists (L words per lane, lane stride 32), UNR words per step;
-// word it always goes to chain it % 2 (the sum is the same for every UNR and both loops, bit
-// for bit).  Schedule in shared memory: the next step's words are loaded while the current ones
-// are used (1.03x at level 20).  Schedule in global memory (GSCH): words read through the
-// read-only path, one step at a time (loading a step ahead measured 1.5x slower at level 24;
-// an L1 prefetch 8-64 rows ahead and the barrier interval changed nothing).
-template <int NB, bool INL, int UNR, bool GSCH = false>
+// one round of 32 destination lists (L words per lane, lane stride 32) from a schedule in shared
+// memory, UNR words per step, the next step's words loaded while the current ones are used;
+// word it always goes to chain it % 2 (the sum is the same for every UNR, and for the streamed
+// variant below, bit for bit)
+template <int NB, bool INL, int UNR>
 __device__ __forceinline__ void slab_round(const uint32_t* slab, int L, const float* coef, float* const (&v)[NB],
                                            float* const (&w)[NB], float (&acc)[NB]) {
   static_assert(UNR % 2 == 0, "whole pairs of words per iteration");
@@ -325,33 +323,104 @@ __device__ __forceinline__ void slab_round(const uint32_t* slab, int L, const fl
 #pragma unroll
     for (int j = 0; j < NB; ++j) a[u][j] = 0.f;
   const int LU = L - L % UNR;   // rows of the whole steps
-  if constexpr (GSCH) {
-    for (int it = 0; it < LU; it += UNR) {
+  uint32_t nxt[UNR];
+  if (LU > 0) {
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) nxt[u] = slab[32 * u];
+  }
+  for (int it = 0; it < LU; it += UNR) {
+    uint32_t wd[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) wd[u] = nxt[u];
+    if (it + UNR < LU) {
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) nxt[u] = slab[32 * (it + UNR + u)];
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u & 1]);
+  }
+  for (int it = LU; it < L; ++it) slab_term<NB, INL>(slab[32 * it], coef, v, w, a[it & 1]);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) acc[j] += a[0][j] + a[1][j];
+}
+
+// Streamed schedule (a level whose schedule does not fit shared memory beside the value
+// arrays): the forward and reverse slabs, one after the other, form a stream of rows (32 words,
+// 128 B each) that repeats for every neighborhood iteration, padded to whole chunks of kCR rows.
+// The block's threads copy chunk c into ring slot c % kRing with cp.async while chunk c - 1 is
+// in use; every warp walks the same rows, so at the first row of chunk k all of them meet,
+// wait for its copies, and start the copy of chunk k + kRing - 1 into the slot just freed.
+constexpr int kCR = 32;     // rows per chunk (4 KB)
+constexpr int kRing = 2;    // chunks in the ring
+__host__ __device__ constexpr size_t ring_bytes() { return static_cast<size_t>(kRing) * kCR * 32 * 4; }
+
+struct Stream {
+  uint32_t* ring;
+  const uint32_t* fsl;   // forward slab rows [0, FR), then reverse slab rows [FR, TR)
+  const uint32_t* rsl;
+  int FR, TR, TRp;       // TRp: TR rounded up to whole chunks
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// copy chunk c of the stream into its ring slot (all threads of the block; one commit group)
+__device__ __forceinline__ void issue_chunk(const Stream& S, long long c) {
+  const int local = static_cast<int>((c * kCR) % S.TRp);
+  uint32_t* dst = S.ring + static_cast<int>(c % kRing) * kCR * 32;
+  for (int u = threadIdx.x; u < kCR * 8; u += blockDim.x) {
+    const int row = local + (u >> 3), l4 = (u & 7) * 4;
+    const uint32_t* src = row < S.FR ? S.fsl + 32 * row + l4 : (row < S.TR ? S.rsl + 32 * (row - S.FR) + l4 : nullptr);
+    if (src) cp_async16(dst + (u >> 3) * 32 + l4, src);
+  }
+  cp_async_commit();
+}
+
+// the round starting at stream row R0 (of this iteration's rows), L rows
+template <int NB, bool INL, int UNR>
+__device__ __forceinline__ void slab_round_stream(const Stream& S, long long R0, int L, int lane, const float* coef,
+                                                  float* const (&v)[NB], float* const (&w)[NB], float (&acc)[NB]) {
+  static_assert(UNR % 2 == 0, "whole pairs of words per iteration");
+  float a[2][NB];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a[u][j] = 0.f;
+  int it = 0;
+  while (it < L) {
+    const long long R = R0 + it;
+    const int off = static_cast<int>(R % kCR);
+    if (off == 0) {   // the first row of chunk k = R / kCR: the same point for every warp
+      cp_async_wait<kRing - 2>();
+      __syncthreads();
+      issue_chunk(S, R / kCR + kRing - 1);
+    }
+    const int end = it + min(L - it, kCR - off);
+    // rows it .. end - 1 of the round are rows off .. of the chunk's slot
+    const uint32_t* slab = S.ring + static_cast<int>((R / kCR) % kRing) * kCR * 32 + (off - it) * 32 + lane;
+    if ((it & 1) && it < end) {   // an odd first row: chains stay those of the round's row index
+      slab_term<NB, INL>(slab[32 * it], coef, v, w, a[1]);
+      ++it;
+    }
+    for (; it + UNR <= end; it += UNR) {
       uint32_t wd[UNR];
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) wd[u] = __ldg(slab + 32 * (it + u));
+      for (int u = 0; u < UNR; ++u) wd[u] = slab[32 * (it + u)];
 #pragma unroll
       for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u & 1]);
     }
-    for (int it = LU; it < L; ++it) slab_term<NB, INL>(__ldg(slab + 32 * it), coef, v, w, a[it & 1]);
-  } else {
-    uint32_t nxt[UNR];
-    if (LU > 0) {
+    // fewer than UNR rows left, from an even row: chains 0, 1, 0, ...
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) nxt[u] = slab[32 * u];
-    }
-    for (int it = 0; it < LU; it += UNR) {
-      uint32_t wd[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) wd[u] = nxt[u];
-      if (it + UNR < LU) {
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) nxt[u] = slab[32 * (it + UNR + u)];
+    for (int u = 0; u < UNR - 1; ++u)
+      if (it < end) {
+        slab_term<NB, INL>(slab[32 * it], coef, v, w, a[u & 1]);
+        ++it;
       }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u & 1]);
-    }
-    for (int it = LU; it < L; ++it) slab_term<NB, INL>(slab[32 * it], coef, v, w, a[it & 1]);
   }
 #pragma unroll
   for (int j = 0; j < NB; ++j) acc[j] += a[0][j] + a[1][j];
@@ -374,15 +443,12 @@ __device__ __forceinline__ void group_combine(float (&acc)[NB], int ent) {
 
 // PRE: moment components per lane prefetched in registers (n_mom <= 32 PRE).  GSCH: the schedule
 // stays in global memory (a level whose schedule does not fit shared memory next to the value
-// arrays): the block's warps meet at a barrier every round, so that they walk the schedule
-// together and each round's words are fetched from L2 once per block and then hit in L1; every
-// warp of a block runs the same number of neighborhood iterations (a warp past the end computes
-// on zeros and writes nothing).
-#ifndef MTP_GSCH_SYNC
-#define MTP_GSCH_SYNC 1   // rounds between the block's barriers in the global-schedule variant
-#endif
+// arrays): the slab words are streamed through a two-chunk ring in shared memory (Stream above),
+// the round headers and lane entries read from global memory (L1) a round ahead; every warp of
+// a block runs the same number of neighborhood iterations (a warp past the end computes on zeros
+// and writes nothing), so that all of them reach every chunk boundary.
 template <int NB, bool INL, int UNR, int PRE, bool GSCH>
-__global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
+__global__ void __launch_bounds__(GSCH ? 256 : 512, 1) k_contract(SplitArgs P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
   const int NV = P.NV;
@@ -396,7 +462,14 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   const int4* s_rround;
   const int* s_rrval;
   const float* s_seed;
+  Stream S{};
   if constexpr (GSCH) {
+    S.ring = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
+    S.fsl = d.pfslab;
+    S.rsl = d.prslab;
+    S.FR = d.pfslab_words / 32;
+    S.TR = S.FR + d.prslab_words / 32;
+    S.TRp = (S.TR + kCR - 1) / kCR * kCR;
     s_fslab = d.pfslab;
     s_fround = reinterpret_cast<const int4*>(d.pfround);
     s_frdst = d.pfr_dst;
@@ -424,7 +497,7 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // per warp: NB (values, adjoints) array pairs, each adjoint array NV after its values
-  float* const wbase = reinterpret_cast<float*>(smem + P.c_bytes + (GSCH ? 0 : P.sched_bytes) + warp * P.warp_bytes);
+  float* const wbase = reinterpret_cast<float*>(smem + P.c_bytes + (GSCH ? ring_bytes() : P.sched_bytes) + warp * P.warp_bytes);
   for (int k = lane; k < 2 * NB * NV; k += 32) wbase[k] = 0.f;   // the zero slot n_vals stays 0
   float* v[NB];
   float* g[NB];
@@ -464,7 +537,12 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
   int64_t w0 = bfirst + static_cast<int64_t>(warp) * NB;
   if (w0 < P.n_work) fetch(w0);
   __syncthreads();
-  for (int64_t b0 = bfirst; GSCH ? b0 < P.n_work : w0 < P.n_work; b0 += stride, w0 += stride) {
+  long long vbase = 0;   // GSCH: the stream row of this iteration's first row
+  if constexpr (GSCH) {
+#pragma unroll
+    for (int c = 0; c < kRing - 1; ++c) issue_chunk(S, c);
+  }
+  for (int64_t b0 = bfirst; GSCH ? b0 < P.n_work : w0 < P.n_work; b0 += stride, w0 += stride, vbase += S.TRp) {
     int64_t wk[NB];
     bool live[NB];
 #pragma unroll
@@ -481,9 +559,6 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
     int4 rd_n = d.n_pfround > 0 ? s_fround[0] : make_int4(0, 0, 0, 0);
     int dst_n = d.n_pfround > 0 ? s_frdst[lane] : -1;
     for (int r = 0; r < d.n_pfround; ++r) {
-      if constexpr (GSCH && MTP_GSCH_SYNC > 0) {
-        if (r % MTP_GSCH_SYNC == 0) __syncthreads();
-      }
       int4 rd = rd_n;
       const int ent = dst_n;
       if (r + 1 < d.n_pfround) {
@@ -494,7 +569,8 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
       float acc[NB];
 #pragma unroll
       for (int j = 0; j < NB; ++j) acc[j] = 0.f;
-      slab_round<NB, INL, UNR, GSCH>(s_fslab + rd.y + lane, rd.x, coef, v, v, acc);
+      if constexpr (GSCH) slab_round_stream<NB, INL, UNR>(S, vbase + (rd.y >> 5), rd.x, lane, coef, v, v, acc);
+      else slab_round<NB, INL, UNR>(s_fslab + rd.y + lane, rd.x, coef, v, v, acc);
       if (rd.w) group_combine<NB>(acc, ent);
       const int dst = ent & 0xffff;
       if (ent >= 0 && ((ent >> 20) & 1) && OK(dst, NV, 26)) {
@@ -521,9 +597,6 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
     int x_n = d.n_prround > 0 ? s_rrval[lane] : -1;
     int x_nn = d.n_prround > 1 ? s_rrval[32 + lane] : -1;
     for (int r = 0; r < d.n_prround; ++r) {
-      if constexpr (GSCH && MTP_GSCH_SYNC > 0) {
-        if (r % MTP_GSCH_SYNC == 0) __syncthreads();
-      }
       int4 rd = rd_n;
       const int ent = x_n;
       if (r + 1 < d.n_prround) {
@@ -538,7 +611,8 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
       float acc[NB];
 #pragma unroll
       for (int j = 0; j < NB; ++j) acc[j] = sd;
-      slab_round<NB, INL, UNR, GSCH>(s_rslab + rd.y + lane, rd.x, coef, v, g, acc);
+      if constexpr (GSCH) slab_round_stream<NB, INL, UNR>(S, vbase + S.FR + (rd.y >> 5), rd.x, lane, coef, v, g, acc);
+      else slab_round<NB, INL, UNR>(s_rslab + rd.y + lane, rd.x, coef, v, g, acc);
       if (rd.w) group_combine<NB>(acc, ent);
       if (lead && OK(x, NV, 32)) {
 #pragma unroll
@@ -577,6 +651,7 @@ __global__ void __launch_bounds__(512) k_contract(SplitArgs P) {
     }
     __syncwarp();
   }
+  if constexpr (GSCH) cp_async_wait<0>();   // the chunks copied ahead of the last rows
 }
 
 // ------------------------------------------------------------------------------------
@@ -774,9 +849,9 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool
   }
   // ---- contraction ----
   {
-    const size_t sched = gsch ? 0 : P.sched_bytes;
+    const size_t sched = gsch ? ring_bytes() : P.sched_bytes;
     const int wpb = std::max(1, static_cast<int>((227 * 1024 - P.c_bytes - sched) / P.warp_bytes));
-    const int warps = std::min(wpb, 16);
+    const int warps = std::min(wpb, gsch ? 8 : 16);   // the streamed variant is built for <= 256 threads
     const bool inl = P.d.coef_inline;
     auto launch = [&](auto kern) {
       const size_t sm = P.c_bytes + sched + static_cast<size_t>(warps) * P.warp_bytes;
@@ -904,8 +979,9 @@ bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const 
   // global memory is asked for), else read from global memory (level 24: 0.4 MB of slab words)
   const bool gsch = P.c_bytes + P.sched_bytes + 4 * P.warp_bytes > 227 * 1024 || m->tune_split_gsch == 2;
   if ((nr >= 6 && !gsch) || (nr >= 6 && d.coef_inline)) return false;
-  if (P.c_bytes + (gsch ? 0 : P.sched_bytes) + P.warp_bytes > 227 * 1024) return false;
-  P.total = P.c_bytes + (gsch ? 0 : P.sched_bytes) + P.warp_bytes;
+  if (gsch && (d.pfslab_words % 32 != 0 || d.prslab_words % 32 != 0)) return false;   // whole rows
+  if (P.c_bytes + (gsch ? ring_bytes() : P.sched_bytes) + P.warp_bytes > 227 * 1024) return false;
+  P.total = P.c_bytes + (gsch ? ring_bytes() : P.sched_bytes) + P.warp_bytes;
   const int wp = m->tune_split_warps > 0 ? m->tune_split_warps : 8;
   m->last_fast = true;
   m->last_split = true;
