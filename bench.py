@@ -64,8 +64,8 @@ COMPANION = {"seed": 444, "cells": 8, "eps": 1e-2}
 MEASURED_TRAFFIC = {
     # the three kernels of the split per-neighborhood pass (k_moments + k_contract + k_adjoint)
     "site_pass": {"source": "paper_2304_13144_gb300/csrc/site_split.cu",
-                  "sha1": "40888aa8d9f22390c28f669112406c36949a519d",
-                  "atoms": 131072, "bytes": (119737088 + 103470336) + (163433984 + 401169152) + (294975488 + 422897408)},
+                  "sha1": "3fe540004ee60656987bf88c868b5d05010d2c49",
+                  "atoms": 131072, "bytes": (119731456 + 103085568) + (163373056 + 401205248) + (294474240 + 422961920)},
     "grade_tc_tf32x3": {"source": "paper_2304_13144_gb300/csrc/grade_tc.cu",
                         "sha1": "62e17e87b10aee78ab8b421d2404bd3a45d54efa",
                         "atoms": 131072, "bytes": 507654656 + 2607872},
@@ -307,6 +307,9 @@ def run_ours(args):
     measured = measure_peaks(api) if not args.no_peaks else None
     if args.cells and args.config == "C4":
         bnp = synth.fcc_ternary(seed=w.input_seed + rank, n=args.cells)   # smaller C4 cells (profiling)
+    elif args.cells and args.config == "C5":
+        # the 32,768-atom liquid cube repeated cells^3 times instead of 4^3 (profiling)
+        bnp = synth.liquid_rsa(seed=w.input_seed + rank, n_atoms=32768 * args.cells ** 3, tiles=args.cells)
     else:
         bnp = w.inputs(w.input_seed + rank)
     desc, theta = w.desc(), w.theta()
@@ -810,7 +813,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes (fixed launch sequence)")
     ap.add_argument("--split-shape", default="",
                     help="warps_pair,nb_contract[,unroll[,schedule]] of the three-kernel pass (no autotune)")
-    ap.add_argument("--cells", type=int, default=0, help="C4 only: n^3 fcc cells instead of 64^3 (profiling)")
+    ap.add_argument("--cells", type=int, default=0,
+                    help="C4: n^3 fcc cells instead of 64^3; C5: the liquid cube repeated n^3 times instead of 4^3 (profiling)")
     ap.add_argument("--mixed-pass", default="auto", choices=["auto", "single", "split"],
                     help="mixed path: the autotuner's choice, the single kernel or the three kernels")
     ap.add_argument("--ref-sample", type=int, default=256)
