@@ -612,7 +612,7 @@ def run_ours(args):
         "roofline_kernels": {k: roof_of(k) for k in per_step if k in work and k != dominant and roof_of(k)},
         "mixed_pass": dict(zip(("setting", "in_use", "split_warps", "split_nb"), api.mtp_get_mixed_pass(model)),
                            requested=args.mixed_pass,
-                           **dict(zip(("split_unroll", "split_schedule", "split_schedule_global"),
+                           **dict(zip(("split_unroll", "split_schedule", "split_schedule_used"),
                                       api.mtp_get_split_shape(model)[2:]))),
         "measured_peaks": measured, "kernels": kernels, "gpu_launches": launches, "clocks": clk,
         "e2e": e2e,

@@ -342,17 +342,20 @@ mtp_status mtp_set_mixed_pass(mtp_model* model, int pass);
 
 /* Launch shape of the three-kernel pass (what mtp_autotune sets): warps per block of its
  * per-pair kernels (4 or 8; 0 = default 8), neighborhoods per warp of its contraction (1 or 2;
- * 0 = default 1), schedule words in flight per lane there (2 or 4; 0 = default 2) and where the
- * contraction reads its schedule (1 = shared memory, 2 = global memory through L1 with the
- * block's warps in step, 0 = shared memory where it fits beside four warps' value arrays; a
- * schedule that does not fit is always read from global memory).  Results do not depend on it.
- * MTP_ERR_ARG outside these values.  No GPU work. */
+ * 0 = default 1), schedule words per step per lane there (2 or 4, or 8 with two neighborhoods per
+ * warp; 0 = default 2) and where the
+ * contraction reads its schedule (1 = shared memory; 2 = streamed from global memory through a
+ * shared-memory ring, the block's warps in step; 3 = tensor memory, the first 512 rows of 128 B,
+ * the rest in shared memory; 0 = shared memory where it fits beside four warps' value arrays).
+ * A schedule that fits neither shared nor tensor memory is always streamed; a placement that
+ * does not apply falls back to the automatic one.  Results do not depend on it.  MTP_ERR_ARG
+ * outside these values.  No GPU work. */
 mtp_status mtp_set_split_shape(mtp_model* model, int warps_pair, int nb_contract, int unroll, int schedule);
 
-/* The shape set above (or by mtp_autotune), HOST outputs, any may be NULL; *schedule_global is
- * where the last three-kernel pass read its schedule (1 = global memory, 0 = shared memory). */
+/* The shape set above (or by mtp_autotune), HOST outputs, any may be NULL; *schedule_used is
+ * where the last three-kernel pass read its schedule (1, 2 or 3 as above; 0 before any). */
 mtp_status mtp_get_split_shape(const mtp_model* model, int32_t* warps_pair, int32_t* nb_contract, int32_t* unroll,
-                               int32_t* schedule, int32_t* schedule_global);
+                               int32_t* schedule, int32_t* schedule_used);
 
 /* The setting above, the pass the next mixed call will run (1 or 2), and the three-kernel
  * pass's tuned shape (warps per block of its per-pair kernels, neighborhoods per warp of its

@@ -527,12 +527,12 @@ def mtp_set_mixed_pass(model, p):
 
 
 def mtp_set_split_shape(model, warps_pair=0, nb_contract=0, unroll=0, schedule=0):
-    """schedule: 0 automatic, 1 shared memory, 2 global memory (the contraction's schedule)."""
+    """schedule: 0 automatic, 1 shared memory, 2 streamed through a shared ring, 3 tensor memory."""
     _check(lib().mtp_set_split_shape(model.h, int(warps_pair), int(nb_contract), int(unroll), int(schedule)))
 
 
 def mtp_get_split_shape(model):
-    """(warps_pair, nb_contract, unroll, schedule setting, last pass read the schedule from global memory)."""
+    """(warps_pair, nb_contract, unroll, schedule setting, placement the last pass used: 1, 2 or 3)."""
     v = [ctypes.c_int32() for _ in range(5)]
     _check(lib().mtp_get_split_shape(model.h, *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)

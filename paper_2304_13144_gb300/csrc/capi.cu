@@ -838,16 +838,18 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
     md->mixed_pass = keep_pass;
     if (split_ok) {
       md->tune_split = 1;
-      for (int sg : {1, 2})
+      for (int sg : {1, 2, 3})
       for (int sw : {4, 8})
-        for (int sc : {12, 14, 22, 24}) {
+        for (int sc : {12, 14, 22, 24, 28}) {
           const int snb = sc / 10, sun = sc % 10;
+          // level 24 (6 radial functions): only the streamed schedule applies
+          if (md->ds.n_rad >= 6 && (sg != 2 || sun == 8)) continue;
           md->tune_split_warps = sw;
           md->tune_split_nb = snb;
           md->tune_split_unroll = sun;
-          md->tune_split_gsch = sg;
+          md->tune_split_sched = sg;
           run();
-          if (!md->last_split || static_cast<int>(md->last_split_gsch) + 1 != sg) continue;   // placement unavailable
+          if (!md->last_split || md->last_split_sched != sg) continue;   // placement unavailable
           float t_min = 0.f;
           for (int rep = 0; rep < 3; ++rep) {
             MTP_CUDA(cudaEventRecord(e0, s));
@@ -872,7 +874,7 @@ mtp_status mtp_autotune(mtp_model* md, const mtp_batch* b, const mtp_nbr* nb, mt
       md->tune_split_warps = best_sw;
       md->tune_split_nb = best_snb;
       md->tune_split_unroll = best_sun;
-      md->tune_split_gsch = best_sg;
+      md->tune_split_sched = best_sg;
       const bool split = md->mixed_pass == 2 || best_split < best_ms;
       if (md->mixed_pass == 0) md->tune_split = split ? 1 : 0;
       if (split) best_ms = best_split;
@@ -907,24 +909,24 @@ mtp_status mtp_set_split_shape(mtp_model* md, int warps_pair, int nb_contract, i
     check_model(md);
     if (warps_pair != 0 && warps_pair != 4 && warps_pair != 8) throw Fail{MTP_ERR_ARG, "warps_pair must be 0, 4 or 8"};
     if (nb_contract < 0 || nb_contract > 2) throw Fail{MTP_ERR_ARG, "nb_contract must be 0, 1 or 2"};
-    if (unroll != 0 && unroll != 2 && unroll != 4) throw Fail{MTP_ERR_ARG, "unroll must be 0, 2 or 4"};
-    if (schedule < 0 || schedule > 2) throw Fail{MTP_ERR_ARG, "schedule must be 0, 1 or 2"};
+    if (unroll != 0 && unroll != 2 && unroll != 4 && unroll != 8) throw Fail{MTP_ERR_ARG, "unroll must be 0, 2, 4 or 8"};
+    if (schedule < 0 || schedule > 3) throw Fail{MTP_ERR_ARG, "schedule must be 0, 1, 2 or 3"};
     md->tune_split_warps = warps_pair;
     md->tune_split_nb = nb_contract;
     md->tune_split_unroll = unroll;
-    md->tune_split_gsch = schedule;
+    md->tune_split_sched = schedule;
   });
 }
 
 mtp_status mtp_get_split_shape(const mtp_model* md, int32_t* warps_pair, int32_t* nb_contract, int32_t* unroll,
-                               int32_t* schedule, int32_t* schedule_global) {
+                               int32_t* schedule, int32_t* schedule_used) {
   return guarded([&] {
     if (!md) throw Fail{MTP_ERR_ARG, "null model"};
     if (warps_pair) *warps_pair = md->tune_split_warps;
     if (nb_contract) *nb_contract = md->tune_split_nb;
     if (unroll) *unroll = md->tune_split_unroll;
-    if (schedule) *schedule = md->tune_split_gsch;
-    if (schedule_global) *schedule_global = md->last_split_gsch ? 1 : 0;
+    if (schedule) *schedule = md->tune_split_sched;
+    if (schedule_used) *schedule_used = md->last_split_sched;
   });
 }
 

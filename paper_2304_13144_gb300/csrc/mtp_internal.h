@@ -204,10 +204,10 @@ struct mtp_model {
   int tune_split_warps = 0;
   int tune_split_nb = 0;
   int tune_split_unroll = 0;   // words in flight per lane in the contraction (2 or 4; 0 = 2)
-  int tune_split_gsch = 0;     // contraction schedule: 0 = shared memory where it fits, 1 = shared
-                               // memory, 2 = global memory
+  int tune_split_sched = 0;    // contraction schedule: 0 = shared memory where it fits, 1 = shared
+                               // memory, 2 = streamed through a shared ring, 3 = tensor memory
   bool last_split = false;
-  bool last_split_gsch = false;   // the last three-kernel pass read its schedule from global memory
+  int last_split_sched = 0;   // where the last three-kernel pass read its schedule (1, 2 or 3 as above)
   mtp::DevBuf split_tab;       // slot -> component table of the split pass (uploaded by mtp_load)
   mtp::DevBuf ws_mom;          // moments / their adjoints of the split pass
 };

@@ -70,6 +70,7 @@ struct SplitArgs {
   int T, CBN, NC, NV;
   // contraction kernel: shared-memory layout (word offsets of the schedule arrays)
   size_t c_bytes, sched_bytes, warp_bytes, total;
+  size_t ovf_bytes;   // schedule in tensor memory: the stream rows past its 512 columns
   int o_fslab, o_fround, o_frdst, o_rslab, o_rround, o_rrval, o_seed;
 };
 
@@ -426,6 +427,90 @@ __device__ __forceinline__ void slab_round_stream(const Stream& S, long long R0,
   for (int j = 0; j < NB; ++j) acc[j] += a[0][j] + a[1][j];
 }
 
+// Schedule in tensor memory (a level whose slab stream has few rows beyond 512): the first
+// kTmemRows rows of the stream (forward slab rows, then reverse slab rows) sit in the block's
+// 512 TMEM columns, row r in column r, lane l of the row in TMEM lane 32 q + l of every lane
+// quarter q (a warp reads the quarter of its warp index mod 4); rows past them in shared memory.
+// This leaves shared memory to the value arrays (two neighborhoods per warp, 12 warps at level
+// 20).  Words are read with tcgen05.ld (32 lanes x 32 bit, one column), the next step's in
+// flight while the current step's are used; tcgen05.wait::ld names the loaded registers, so no
+// use of them is scheduled before it.
+constexpr int kTmemRows = 512;
+
+template <int N>
+__device__ __forceinline__ void tmem_ld_rows(uint32_t taddr, uint32_t (&w)[N]) {
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(w[u]) : "r"(taddr + u) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void tmem_wait_rows(uint32_t (&w)[N]) {
+  if constexpr (N == 1) asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(w[0])::"memory");
+  else if constexpr (N == 2) asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(w[0]), "+r"(w[1])::"memory");
+  else if constexpr (N == 4)
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3])::"memory");
+  else if constexpr (N == 8)
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]), "+r"(w[6]), "+r"(w[7])::"memory");
+  else static_assert(N == 1 || N == 2 || N == 4 || N == 8, "steps of 1, 2, 4 or 8 words");
+}
+
+// the round starting at stream row R0, L rows: rows below kTmemRows from TMEM (tq = the TMEM
+// address of column 0 in this warp's lane quarter), the others from `ovf` (shared memory, row
+// kTmemRows first, this lane's word at ovf[32 (row - kTmemRows)])
+template <int NB, bool INL, int UNR>
+__device__ __forceinline__ void slab_round_tmem(uint32_t tq, const uint32_t* ovf, int R0, int L, const float* coef,
+                                                float* const (&v)[NB], float* const (&w)[NB], float (&acc)[NB]) {
+  static_assert(UNR % 2 == 0, "whole pairs of words per iteration");
+  float a[2][NB];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a[u][j] = 0.f;
+  const int Lt = max(0, min(L, kTmemRows - R0));   // rows in tensor memory
+  const int LU = Lt - Lt % UNR;
+  if (LU > 0) {
+    uint32_t nxt[UNR];
+    tmem_ld_rows<UNR>(tq + R0, nxt);
+    tmem_wait_rows<UNR>(nxt);
+    for (int it = 0; it < LU; it += UNR) {
+      uint32_t wd[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) wd[u] = nxt[u];
+      const bool more = it + UNR < LU;
+      if (more) tmem_ld_rows<UNR>(tq + R0 + it + UNR, nxt);
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) slab_term<NB, INL>(wd[u], coef, v, w, a[u & 1]);
+      if (more) tmem_wait_rows<UNR>(nxt);
+    }
+  }
+  int it = LU;
+#pragma unroll
+  for (int u = 0; u < UNR - 1; ++u)   // fewer than UNR rows left, from an even row: chains 0, 1, 0
+    if (it < Lt) {
+      uint32_t t1[1];
+      tmem_ld_rows<1>(tq + R0 + it, t1);
+      tmem_wait_rows<1>(t1);
+      slab_term<NB, INL>(t1[0], coef, v, w, a[u & 1]);
+      ++it;
+    }
+  if (it < L) {   // rows past tensor memory
+    const uint32_t* slab = ovf + 32 * (R0 - kTmemRows);
+    if ((it & 1) && it < L) {
+      slab_term<NB, INL>(slab[32 * it], coef, v, w, a[1]);
+      ++it;
+    }
+    for (; it + 2 <= L; it += 2) {
+      const uint32_t w0 = slab[32 * it], w1 = slab[32 * (it + 1)];
+      slab_term<NB, INL>(w0, coef, v, w, a[0]);
+      slab_term<NB, INL>(w1, coef, v, w, a[1]);
+    }
+    if (it < L) slab_term<NB, INL>(slab[32 * it], coef, v, w, a[0]);
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) acc[j] += a[0][j] + a[1][j];
+}
+
 // partial sums of a list split over an aligned group of 2^lg lanes (lane entry bits 16..19):
 // after the butterfly every lane of the group holds the group's total (idle lanes: garbage)
 template <int NB>
@@ -447,8 +532,10 @@ __device__ __forceinline__ void group_combine(float (&acc)[NB], int ent) {
 // the round headers and lane entries read from global memory (L1) a round ahead; every warp of
 // a block runs the same number of neighborhood iterations (a warp past the end computes on zeros
 // and writes nothing), so that all of them reach every chunk boundary.
-template <int NB, bool INL, int UNR, int PRE, bool GSCH>
-__global__ void __launch_bounds__(GSCH ? 256 : 512, 1) k_contract(SplitArgs P) {
+template <int NB, bool INL, int UNR, int PRE, int SCH>
+__global__ void __launch_bounds__(SCH == 1 ? 256 : 512, 1) k_contract(SplitArgs P) {
+  constexpr bool GSCH = SCH == 1;   // streamed through the shared ring
+  constexpr bool TMS = SCH == 2;    // in tensor memory
   extern __shared__ __align__(16) unsigned char smem[];
   const DevSchedule& d = P.d;
   const int NV = P.NV;
@@ -463,13 +550,50 @@ __global__ void __launch_bounds__(GSCH ? 256 : 512, 1) k_contract(SplitArgs P) {
   const int* s_rrval;
   const float* s_seed;
   Stream S{};
-  if constexpr (GSCH) {
-    S.ring = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
-    S.fsl = d.pfslab;
-    S.rsl = d.prslab;
-    S.FR = d.pfslab_words / 32;
-    S.TR = S.FR + d.prslab_words / 32;
-    S.TRp = (S.TR + kCR - 1) / kCR * kCR;
+  __shared__ uint32_t tmem_slot;
+  uint32_t tq = 0;              // TMS: TMEM address of column 0 in this warp's lane quarter
+  const uint32_t* ovf = nullptr;   // TMS: stream rows past tensor memory (this lane's word)
+  if constexpr (TMS) {
+    const int nw = blockDim.x >> 5, wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    if (wp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       static_cast<unsigned>(__cvta_generic_to_shared(&tmem_slot))),
+                   "r"(512));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int FR = d.pfslab_words / 32, TR = FR + d.prslab_words / 32, TT = min(TR, kTmemRows);
+    const int q = wp & 3;
+    tq = tmem_slot + (static_cast<uint32_t>(32 * q) << 16);
+    // the warps of lane quarter q write its copy of rows [0, TT), one column per store
+    const int nq = (nw - q + 3) / 4, kq = wp >> 2;
+    for (int r = kq; r < TT; r += nq) {
+      const uint32_t word = r < FR ? d.pfslab[32 * r + ln] : d.prslab[32 * (r - FR) + ln];
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(tq + r), "r"(word) : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    uint32_t* o = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
+    for (int k = threadIdx.x; k < 32 * (TR - TT); k += blockDim.x) {
+      const int r = TT + k / 32;
+      o[k] = r < FR ? d.pfslab[32 * r + (k & 31)] : d.prslab[32 * (r - FR) + (k & 31)];
+    }
+    ovf = o + ln;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    S.FR = FR;
+  }
+  if constexpr (GSCH || TMS) {
+    if constexpr (GSCH) {
+      S.ring = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
+      S.fsl = d.pfslab;
+      S.rsl = d.prslab;
+      S.FR = d.pfslab_words / 32;
+      S.TR = S.FR + d.prslab_words / 32;
+      S.TRp = (S.TR + kCR - 1) / kCR * kCR;
+    }
     s_fslab = d.pfslab;
     s_fround = reinterpret_cast<const int4*>(d.pfround);
     s_frdst = d.pfr_dst;
@@ -497,7 +621,9 @@ __global__ void __launch_bounds__(GSCH ? 256 : 512, 1) k_contract(SplitArgs P) {
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // per warp: NB (values, adjoints) array pairs, each adjoint array NV after its values
-  float* const wbase = reinterpret_cast<float*>(smem + P.c_bytes + (GSCH ? ring_bytes() : P.sched_bytes) + warp * P.warp_bytes);
+  float* const wbase =
+      reinterpret_cast<float*>(smem + P.c_bytes + (GSCH ? ring_bytes() : (TMS ? P.ovf_bytes : P.sched_bytes)) +
+                               warp * P.warp_bytes);
   for (int k = lane; k < 2 * NB * NV; k += 32) wbase[k] = 0.f;   // the zero slot n_vals stays 0
   float* v[NB];
   float* g[NB];
@@ -570,6 +696,7 @@ __global__ void __launch_bounds__(GSCH ? 256 : 512, 1) k_contract(SplitArgs P) {
 #pragma unroll
       for (int j = 0; j < NB; ++j) acc[j] = 0.f;
       if constexpr (GSCH) slab_round_stream<NB, INL, UNR>(S, vbase + (rd.y >> 5), rd.x, lane, coef, v, v, acc);
+      else if constexpr (TMS) slab_round_tmem<NB, INL, UNR>(tq, ovf, rd.y >> 5, rd.x, coef, v, v, acc);
       else slab_round<NB, INL, UNR>(s_fslab + rd.y + lane, rd.x, coef, v, v, acc);
       if (rd.w) group_combine<NB>(acc, ent);
       const int dst = ent & 0xffff;
@@ -612,6 +739,7 @@ __global__ void __launch_bounds__(GSCH ? 256 : 512, 1) k_contract(SplitArgs P) {
 #pragma unroll
       for (int j = 0; j < NB; ++j) acc[j] = sd;
       if constexpr (GSCH) slab_round_stream<NB, INL, UNR>(S, vbase + S.FR + (rd.y >> 5), rd.x, lane, coef, v, g, acc);
+      else if constexpr (TMS) slab_round_tmem<NB, INL, UNR>(tq, ovf, S.FR + (rd.y >> 5), rd.x, coef, v, g, acc);
       else slab_round<NB, INL, UNR>(s_rslab + rd.y + lane, rd.x, coef, v, g, acc);
       if (rd.w) group_combine<NB>(acc, ent);
       if (lead && OK(x, NV, 32)) {
@@ -652,6 +780,14 @@ __global__ void __launch_bounds__(GSCH ? 256 : 512, 1) k_contract(SplitArgs P) {
     __syncwarp();
   }
   if constexpr (GSCH) cp_async_wait<0>();   // the chunks copied ahead of the last rows
+  if constexpr (TMS) {   // every warp is past its last tensor-memory read
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(512));
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -830,7 +966,7 @@ int num_sms() {
 }
 
 template <int NR, int NU0>
-void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool gsch, bool efs, bool rows,
+void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, int sch, bool efs, bool rows,
                   cudaStream_t s) {
   const int nsm = num_sms();
   const int64_t groups = (P.n_work + GPW - 1) / GPW;
@@ -849,12 +985,15 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool
   }
   // ---- contraction ----
   {
-    const size_t sched = gsch ? ring_bytes() : P.sched_bytes;
+    const size_t sched = sch == 2 ? ring_bytes() : (sch == 3 ? P.ovf_bytes : P.sched_bytes);
     const int wpb = std::max(1, static_cast<int>((227 * 1024 - P.c_bytes - sched) / P.warp_bytes));
-    const int warps = std::min(wpb, gsch ? 8 : 16);   // the streamed variant is built for <= 256 threads
+    const int warps = std::min(wpb, sch == 2 ? 8 : 16);   // the streamed variant is built for <= 256 threads
     const bool inl = P.d.coef_inline;
     auto launch = [&](auto kern) {
-      const size_t sm = P.c_bytes + sched + static_cast<size_t>(warps) * P.warp_bytes;
+      size_t sm = P.c_bytes + sched + static_cast<size_t>(warps) * P.warp_bytes;
+      // a block that holds all 512 tensor-memory columns: more than half the shared memory, so
+      // that no second block shares its SM (it would wait for the columns)
+      if (sch == 3) sm = std::max<size_t>(sm, 120 * 1024);
       MTP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
       const int per = blocks_per_sm(kern, warps * 32, sm);
       const int64_t need = (P.n_work + nb_contract - 1) / nb_contract;
@@ -866,22 +1005,26 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, bool
       MTP_CUDA(cudaGetLastError());
     };
     constexpr int PRE = pre_of(NR);
-    // the level-24 shape (6, 10) only has the global-schedule, 12-bit-index variant (its 3,853
-    // values need 12-bit indices, its schedule does not fit shared memory; the caller checks)
+    // the level-24 shape (6, 10) only has the streamed, 12-bit-index variant (its 3,853 values
+    // need 12-bit indices, its schedule fits neither shared nor tensor memory; the caller checks)
     auto pick = [&](auto nbc, auto unr) {
       constexpr int NBc = decltype(nbc)::value, U = decltype(unr)::value;
       if constexpr (NR >= 6) {
-        launch(k_contract<NBc, false, U, PRE, true>);
-      } else if (gsch) {
-        if (inl) launch(k_contract<NBc, true, U, PRE, true>);
-        else launch(k_contract<NBc, false, U, PRE, true>);
+        launch(k_contract<NBc, false, U, PRE, 1>);
+      } else if (sch == 2) {
+        if (inl) launch(k_contract<NBc, true, U, PRE, 1>);
+        else launch(k_contract<NBc, false, U, PRE, 1>);
+      } else if (sch == 3) {
+        if (inl) launch(k_contract<NBc, true, U, PRE, 2>);
+        else launch(k_contract<NBc, false, U, PRE, 2>);
       } else {
-        if (inl) launch(k_contract<NBc, true, U, PRE, false>);
-        else launch(k_contract<NBc, false, U, PRE, false>);
+        if (inl) launch(k_contract<NBc, true, U, PRE, 0>);
+        else launch(k_contract<NBc, false, U, PRE, 0>);
       }
     };
     if (nb_contract == 2) {
-      if (unroll == 4) pick(std::integral_constant<int, 2>{}, std::integral_constant<int, 4>{});
+      if (unroll == 8 && NR < 6) pick(std::integral_constant<int, 2>{}, std::integral_constant<int, 8>{});
+      else if (unroll == 4) pick(std::integral_constant<int, 2>{}, std::integral_constant<int, 4>{});
       else pick(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{});
     } else {
       if (unroll == 4) pick(std::integral_constant<int, 1>{}, std::integral_constant<int, 4>{});
@@ -977,23 +1120,33 @@ bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const 
   P.warp_bytes = static_cast<size_t>(2 * nbc * P.NV) * sizeof(float);
   // the schedule in shared memory when it fits beside at least four warps' value arrays (unless
   // global memory is asked for), else read from global memory (level 24: 0.4 MB of slab words)
-  const bool gsch = P.c_bytes + P.sched_bytes + 4 * P.warp_bytes > 227 * 1024 || m->tune_split_gsch == 2;
-  if ((nr >= 6 && !gsch) || (nr >= 6 && d.coef_inline)) return false;
-  if (gsch && (d.pfslab_words % 32 != 0 || d.prslab_words % 32 != 0)) return false;   // whole rows
-  if (P.c_bytes + (gsch ? ring_bytes() : P.sched_bytes) + P.warp_bytes > 227 * 1024) return false;
-  P.total = P.c_bytes + (gsch ? ring_bytes() : P.sched_bytes) + P.warp_bytes;
+  // where the contraction reads its schedule: 1 shared memory (when it fits beside at least four
+  // warps' value arrays), 2 streamed through a shared ring (level 24: 0.35 MB of slab words),
+  // 3 tensor memory (the first 512 rows; the rest in shared memory), as asked or automatic
+  const int rows_total = (d.pfslab_words + d.prslab_words) / 32;
+  P.ovf_bytes = static_cast<size_t>(std::max(0, rows_total - kTmemRows)) * 128;
+  const bool fits = P.c_bytes + P.sched_bytes + 4 * P.warp_bytes <= 227 * 1024;
+  const int ask = m->tune_split_sched;
+  int sch = fits ? 1 : 2;
+  if (ask == 2) sch = 2;
+  if (ask == 3 && nr < 6 && P.c_bytes + P.ovf_bytes + 4 * P.warp_bytes <= 227 * 1024) sch = 3;
+  if ((nr >= 6 && sch != 2) || (nr >= 6 && d.coef_inline)) return false;
+  if (sch != 1 && (d.pfslab_words % 32 != 0 || d.prslab_words % 32 != 0)) return false;   // whole rows
+  const size_t sbytes = sch == 2 ? ring_bytes() : (sch == 3 ? P.ovf_bytes : P.sched_bytes);
+  if (P.c_bytes + sbytes + P.warp_bytes > 227 * 1024) return false;
+  P.total = P.c_bytes + sbytes + P.warp_bytes;
   const int wp = m->tune_split_warps > 0 ? m->tune_split_warps : 8;
   m->last_fast = true;
   m->last_split = true;
-  m->last_split_gsch = gsch;
+  m->last_split_sched = sch;
   m->last_warps = wp;
   if (P.n_work == 0) return true;
-  const int unr = m->tune_split_unroll == 4 ? 4 : 2;
-  if (nr == 2) launch_split<2, 2>(P, wp, nbc, unr, gsch, efs, rows, s);
-  else if (nr == 3) launch_split<3, 4>(P, wp, nbc, unr, gsch, efs, rows, s);
-  else if (nr == 4) launch_split<4, 6>(P, wp, nbc, unr, gsch, efs, rows, s);
-  else if (nr == 5) launch_split<5, 8>(P, wp, nbc, unr, gsch, efs, rows, s);
-  else launch_split<6, 10>(P, wp, nbc, unr, gsch, efs, rows, s);
+  const int unr = m->tune_split_unroll == 4 ? 4 : (m->tune_split_unroll == 8 && nbc == 2 ? 8 : 2);
+  if (nr == 2) launch_split<2, 2>(P, wp, nbc, unr, sch, efs, rows, s);
+  else if (nr == 3) launch_split<3, 4>(P, wp, nbc, unr, sch, efs, rows, s);
+  else if (nr == 4) launch_split<4, 6>(P, wp, nbc, unr, sch, efs, rows, s);
+  else if (nr == 5) launch_split<5, 8>(P, wp, nbc, unr, sch, efs, rows, s);
+  else launch_split<6, 10>(P, wp, nbc, unr, sch, efs, rows, s);
 #ifdef MTP_SPLIT_CHECK
   unsigned long long fault = 0;
   MTP_CUDA(cudaStreamSynchronize(s));

@@ -71,22 +71,22 @@ def test_both_mixed_passes_match_oracle(api, lev):
     a, s = outs["single"], outs["split"]
     assert np.abs(a["forces"] - s["forces"]).max() <= 2e-5
     assert np.abs(a["site_virial"] - s["site_virial"]).max() <= 1e-5 * np.abs(a["site_virial"]).max()
-    # the contraction's schedule read from global memory (the block's warps in step) instead of
-    # shared memory, one and two neighborhoods per warp: the same words in the same order, so
-    # bitwise the same results
+    # the contraction's schedule streamed through a shared ring (the block's warps in step) or
+    # held in tensor memory instead of shared memory, one and two neighborhoods per warp, two and
+    # four words per step: the same words in the same order, so bitwise the same results
     api.mtp_set_mixed_pass(model, "split")
-    for nbc in (1, 2):
-        api.mtp_set_split_shape(model, 8, nbc, 2, 2)
+    for sched, nbc, unr in ((2, 1, 2), (2, 2, 2), (3, 1, 2), (3, 2, 2), (3, 2, 4), (3, 2, 8), (1, 2, 8)):
+        api.mtp_set_split_shape(model, 8, nbc, unr, sched)
         o = api.mtp_step(model, b, nb, "mixed", threshold=2.0)
         o.update(api.mtp_energy_forces_stress_atoms(model, b, nb, "mixed"))
-        assert api.mtp_get_split_shape(model)[4] == 1
+        assert api.mtp_get_split_shape(model)[4] == sched
         nf = int(s["n_flagged"][0])
         for k, v in o.items():
             if v is not None and k in s:
                 got, want = v.cpu().numpy(), s[k]
                 if k == "flagged":   # the list is defined up to its count
                     got, want = got[:nf], want[:nf]
-                assert np.array_equal(got, want), (nbc, k)
+                assert np.array_equal(got, want), (sched, nbc, unr, k)
     api.mtp_set_split_shape(model)
     api.mtp_set_mixed_pass(model, "auto")
 
