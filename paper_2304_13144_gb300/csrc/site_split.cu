@@ -533,7 +533,7 @@ __device__ __forceinline__ void group_combine(float (&acc)[NB], int ent) {
 // a block runs the same number of neighborhood iterations (a warp past the end computes on zeros
 // and writes nothing), so that all of them reach every chunk boundary.
 template <int NB, bool INL, int UNR, int PRE, int SCH>
-__global__ void __launch_bounds__(SCH == 1 ? 256 : 512, 1) k_contract(SplitArgs P) {
+__global__ void __launch_bounds__(SCH == 1 ? 256 : (SCH == 2 ? 384 : 512), 1) k_contract(SplitArgs P) {
   constexpr bool GSCH = SCH == 1;   // streamed through the shared ring
   constexpr bool TMS = SCH == 2;    // in tensor memory
   extern __shared__ __align__(16) unsigned char smem[];
@@ -987,7 +987,8 @@ void launch_split(SplitArgs P, int warps_pair, int nb_contract, int unroll, int 
   {
     const size_t sched = sch == 2 ? ring_bytes() : (sch == 3 ? P.ovf_bytes : P.sched_bytes);
     const int wpb = std::max(1, static_cast<int>((227 * 1024 - P.c_bytes - sched) / P.warp_bytes));
-    const int warps = std::min(wpb, sch == 2 ? 8 : 16);   // the streamed variant is built for <= 256 threads
+    // the streamed variant is built for <= 256 threads, the tensor-memory one for <= 384
+    const int warps = std::min(wpb, sch == 2 ? 8 : (sch == 3 ? 12 : 16));
     const bool inl = P.d.coef_inline;
     auto launch = [&](auto kern) {
       size_t sm = P.c_bytes + sched + static_cast<size_t>(warps) * P.warp_bytes;
