@@ -430,9 +430,9 @@ __device__ __forceinline__ void slab_round_stream(const Stream& S, long long R0,
 // Schedule in tensor memory (a level whose slab stream has few rows beyond 512): the first
 // kTmemRows rows of the stream (forward slab rows, then reverse slab rows) sit in the block's
 // 512 TMEM columns, row r in column r, lane l of the row in TMEM lane 32 q + l of every lane
-// quarter q (a warp reads the quarter of its warp index mod 4); rows past them in shared memory.
-// This leaves shared memory to the value arrays (two neighborhoods per warp, 12 warps at level
-// 20).  Words are read with tcgen05.ld (32 lanes x 32 bit, one column), the next step's in
+// quarter q (a warp reads the quarter of its warp index mod 4); rows past them, the round
+// headers, lane entries and seeds in shared memory.  This leaves shared memory to the value
+// arrays (two neighborhoods per warp, 11 warps at level 20).  Words are read with tcgen05.ld (32 lanes x 32 bit, one column), the next step's in
 // flight while the current step's are used; tcgen05.wait::ld names the loaded registers, so no
 // use of them is scheduled before it.
 constexpr int kTmemRows = 512;
@@ -601,6 +601,25 @@ __global__ void __launch_bounds__(SCH == 1 ? 256 : (SCH == 2 ? 384 : 512), 1) k_
     s_rround = reinterpret_cast<const int4*>(d.prround);
     s_rrval = d.prr_val;
     s_seed = d.seed_f;
+    if constexpr (TMS) {
+      // round headers, lane entries and seeds in shared memory after the overflow rows (one warp
+      // fewer than with them read through L1, 13.10 against 13.51 ms at level 20)
+      const int TR = (d.pfslab_words + d.prslab_words) / 32, TT = min(TR, kTmemRows);
+      uint32_t* h = reinterpret_cast<uint32_t*>(smem + P.c_bytes) + 32 * (TR - TT);
+      int o = 0;
+      auto put = [&](const uint32_t* src, int n) {
+        copy_words_s(h + o, src, n);
+        const int at = o;
+        o += (n + 3) & ~3;
+        return h + at;
+      };
+      s_fround = reinterpret_cast<const int4*>(put(reinterpret_cast<const uint32_t*>(d.pfround), 4 * d.n_pfround));
+      s_frdst = reinterpret_cast<const int*>(put(reinterpret_cast<const uint32_t*>(d.pfr_dst), 32 * d.n_pfround));
+      s_rround = reinterpret_cast<const int4*>(put(reinterpret_cast<const uint32_t*>(d.prround), 4 * d.n_prround));
+      s_rrval = reinterpret_cast<const int*>(put(reinterpret_cast<const uint32_t*>(d.prr_val), 32 * d.n_prround));
+      s_seed = reinterpret_cast<const float*>(put(reinterpret_cast<const uint32_t*>(d.seed_f), d.n_vals));
+      __syncthreads();
+    }
   } else {
     uint32_t* sched = reinterpret_cast<uint32_t*>(smem + P.c_bytes);
     copy_words_s(sched + P.o_fslab, d.pfslab, d.pfslab_words);
@@ -1126,6 +1145,8 @@ bool run_sites_split(mtp_model* m, const mtp_batch* b, const mtp_nbr* nb, const 
   // 3 tensor memory (the first 512 rows; the rest in shared memory), as asked or automatic
   const int rows_total = (d.pfslab_words + d.prslab_words) / 32;
   P.ovf_bytes = static_cast<size_t>(std::max(0, rows_total - kTmemRows)) * 128;
+  P.ovf_bytes += static_cast<size_t>(((4 * d.n_pfround + 3) & ~3) + 32 * d.n_pfround + ((4 * d.n_prround + 3) & ~3) +
+                                     32 * d.n_prround + ((d.n_vals + 3) & ~3)) * 4;   // headers, lane entries, seeds
   const bool fits = P.c_bytes + P.sched_bytes + 4 * P.warp_bytes <= 227 * 1024;
   const int ask = m->tune_split_sched;
   int sch = fits ? 1 : 2;
