@@ -64,8 +64,8 @@ COMPANION = {"seed": 444, "cells": 8, "eps": 1e-2}
 MEASURED_TRAFFIC = {
     # the three kernels of the split per-neighborhood pass (k_moments + k_contract + k_adjoint)
     "site_pass": {"source": "paper_2304_13144_gb300/csrc/site_split.cu",
-                  "sha1": "c00c6da3a6cc4119a0de624d8e89aedd5cb578b7",
-                  "atoms": 131072, "bytes": (119718400 + 103074304) + (162960384 + 400337152) + (294511616 + 422898176)},
+                  "sha1": "a96d5804ed0c32be967a076262210f102105bd9e",
+                  "atoms": 131072, "bytes": (119737600 + 103305472) + (162931968 + 400208896) + (294791424 + 422636800)},
     "grade_tc_tf32x3": {"source": "paper_2304_13144_gb300/csrc/grade_tc.cu",
                         "sha1": "62e17e87b10aee78ab8b421d2404bd3a45d54efa",
                         "atoms": 131072, "bytes": 507654656 + 2607872},
